@@ -1,0 +1,220 @@
+"""Pins for the FastPI factorization / solve oracle (Algorithm 1, Eqs. 1-3,
+Problem 1, Application 1).
+
+Every check compares the oracle with something fixed by the paper or by
+mathematics, not with itself:
+  * Problem 1: with r = rank(A) (alpha = 1 here) the pseudoinverse is exact:
+    the four Penrose conditions, the normal equations A^T (A Z - Y) = 0,
+    Z = lstsq(A, Y) when A has full column rank, singular values equal to
+    LAPACK's SVD of the dense A, exact reconstruction A = U Sigma V^T.
+  * closed forms: diagonal A (A^+ = diag(1/d)), rank-1 A = a b^T
+    (A^+ = b a^T / (|a|^2 |b|^2)), 1 x 1 / p x 1 / 1 x q blocks of Eq. 1.
+  * Eq. 1 block-diagonal invariance: the multiset of block singular values is
+    the spectrum of A11.
+  * Eqs. 2 / 3 single shot (dense M and N as printed) equal the incremental
+    form when the whole border is one chunk; at alpha = 1 every chunking gives
+    the exact SVD.
+  * Eckart-Young: no rank-r factorization beats the optimal residual.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads
+from oracle import fastpi, pinv
+from oracle.reorder import reorder
+
+
+def _dense(m, n, rowptr, col, val):
+    return sp.csr_matrix((val, col, rowptr), shape=(m, n)).toarray()
+
+
+def _csr(A):
+    c = sp.csr_matrix(A)
+    c.sort_indices()
+    return c.indptr.astype(np.int64), c.indices.astype(np.int32), c.data.astype(np.float64)
+
+
+def _powerlaw(seed, m=120, n=40, nnz=600, gamma=2.1):
+    rng = np.random.default_rng(seed)
+    return workloads.chung_lu_csr(m, n, nnz, gamma, rng)
+
+
+def test_ceil_alpha():
+    assert fastpi.ceil_alpha(7, 1, 10) == 1        # ceil(0.7)
+    assert fastpi.ceil_alpha(10, 1, 10) == 1
+    assert fastpi.ceil_alpha(11, 1, 10) == 2       # ceil(1.1)
+    assert fastpi.ceil_alpha(0, 3, 10) == 0
+    assert fastpi.ceil_alpha(40, 40, 40) == 40     # alpha = 1
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("chunks", [(None, None), (3, 2), (17, 5)])
+def test_alpha_one_exact_svd_and_penrose(seed, chunks):
+    """alpha = 1: the incremental SVD is exact (r = rank), so A^+ is the Moore-Penrose inverse."""
+    m, n = 120, 40
+    rowptr, col, val = _powerlaw(seed, m, n)
+    A = _dense(m, n, rowptr, col, val)
+    f = fastpi.factor(m, n, rowptr, col, val, r=n, k=0.05, chunk_row=chunks[0], chunk_col=chunks[1])
+    sv = np.linalg.svd(A, compute_uv=False)
+    np.testing.assert_allclose(f.S[:sv.size], sv, rtol=0, atol=1e-12 * sv[0])
+    assert np.linalg.norm(A - (f.U * f.S) @ f.V.T) <= 1e-12 * np.linalg.norm(A)
+    tau = fastpi.pinv_threshold(f.S, m, n)
+    inv = np.where(f.S > tau, 1.0 / np.maximum(f.S, tau), 0.0)
+    X = (f.V * inv) @ f.U.T
+    nA = np.linalg.norm(A)
+    nX = np.linalg.norm(X)
+    assert np.linalg.norm(A @ X @ A - A) <= 1e-10 * nA
+    assert np.linalg.norm(X @ A @ X - X) <= 1e-10 * nX
+    assert np.linalg.norm((A @ X).T - A @ X) <= 1e-10
+    assert np.linalg.norm((X @ A).T - X @ A) <= 1e-10
+    np.testing.assert_allclose(X, pinv.dense_pinv(A), atol=1e-10 * nX)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_alpha_one_lstsq_and_normal_equations(seed):
+    m, n = 150, 30
+    rng = np.random.default_rng(50 + seed)
+    # a dense diagonal guarantees full column rank; extra power-law entries on top
+    rowptr, col, val = _powerlaw(50 + seed, m, n, 500)
+    A = _dense(m, n, rowptr, col, val)
+    A[np.arange(n), np.arange(n)] += 1.0 + rng.random(n)
+    rowptr, col, val = _csr(A)
+    Y = workloads.labels_dense(m, 7, 2, rng)
+    f = fastpi.factor(m, n, rowptr, col, val, r=n, k=0.03, chunk_row=4, chunk_col=3)
+    Z = fastpi.apply(f, Y)
+    Zl = np.linalg.lstsq(A, Y, rcond=None)[0]
+    np.testing.assert_allclose(Z, Zl, atol=1e-10 * np.linalg.norm(Zl))
+    assert np.linalg.norm(A.T @ (A @ Z - Y)) <= 1e-10 * np.linalg.norm(A) * np.linalg.norm(Y)
+
+
+def test_diagonal_matrix_closed_form():
+    d = np.array([3.0, 0.5, 2.0, 7.0, 1.25, 0.1])
+    A = np.zeros((8, 6))
+    A[np.arange(6), np.arange(6)] = d
+    rowptr, col, val = _csr(A)
+    f = fastpi.factor(8, 6, rowptr, col, val, r=6, k=0.2)
+    np.testing.assert_allclose(np.sort(f.S)[::-1], np.sort(d)[::-1], rtol=1e-15)
+    Y = np.eye(8)
+    X = fastpi.apply(f, Y)                       # = A^+
+    Xd = np.zeros((6, 8))
+    Xd[np.arange(6), np.arange(6)] = 1.0 / d
+    np.testing.assert_allclose(X, Xd, atol=1e-14)
+
+
+def test_rank_one_closed_form():
+    rng = np.random.default_rng(3)
+    a = rng.random(9) + 0.1
+    b = rng.random(5) + 0.1
+    A = np.outer(a, b)
+    rowptr, col, val = _csr(A)
+    f = fastpi.factor(9, 5, rowptr, col, val, r=5, k=0.2, chunk_row=2, chunk_col=1)
+    X = fastpi.apply(f, np.eye(9))
+    Xc = np.outer(b, a) / (a @ a * (b @ b))
+    np.testing.assert_allclose(X, Xc, atol=1e-12 * np.linalg.norm(Xc))
+    assert f.S[0] == pytest.approx(np.linalg.norm(a) * np.linalg.norm(b), rel=1e-14)
+    assert np.all(f.S[1:] <= 1e-12 * f.S[0])
+
+
+def test_block_svd_closed_forms_and_invariance():
+    """Eq. 1 on hand-made blocks: 1x1 -> |a|, p x 1 -> column norm, 1 x q -> row norm;
+    untruncated, the block singular values are the spectrum of A11."""
+    m, n = 30, 20
+    rowptr, col, val = _powerlaw(7, m, n, 70)
+    A = _dense(m, n, rowptr, col, val)
+    R = reorder(m, n, rowptr, col, 0.1)
+    _, A11, _, _ = fastpi.split(sp.csr_matrix(A), R)
+    U1, s1, V1, si = fastpi.block_svd(A11, R, r=n, n=n)
+    A11d = A11.toarray()
+    sv = np.linalg.svd(A11d, compute_uv=False) if A11d.size else np.zeros(0)
+    sv = np.sort(sv[sv > 1e-12])[::-1]
+    got = np.sort(s1[s1 > 1e-12])[::-1]
+    np.testing.assert_allclose(got, sv, rtol=1e-13)
+    assert np.linalg.norm(A11d - (U1 * s1) @ V1.T) <= 1e-12 * max(1.0, np.linalg.norm(A11d))
+    ro, co = R.row_off, R.col_off
+    pos = np.concatenate([[0], np.cumsum(si)])
+    for b in range(len(ro) - 1):
+        blk = A11d[ro[b]:ro[b + 1], co[b]:co[b + 1]]
+        if si[b] == 0:
+            continue
+        if blk.shape == (1, 1):
+            assert s1[pos[b]] == pytest.approx(abs(blk[0, 0]), rel=1e-15)
+        elif blk.shape[1] == 1:
+            assert s1[pos[b]] == pytest.approx(np.linalg.norm(blk), rel=1e-14)
+        elif blk.shape[0] == 1:
+            assert s1[pos[b]] == pytest.approx(np.linalg.norm(blk), rel=1e-14)
+
+
+def test_block_truncation_rule():
+    """s_i = min(ceil(alpha n_1i), m_1i, n_1i) with alpha = r / n."""
+    m, n = 200, 60
+    rowptr, col, val = _powerlaw(11, m, n, 500)
+    R = reorder(m, n, rowptr, col, 0.05)
+    A = sp.csr_matrix((val, col, rowptr), shape=(m, n))
+    _, A11, _, _ = fastpi.split(A, R)
+    r = 13
+    _, _, _, si = fastpi.block_svd(A11, R, r=r, n=n)
+    mi, ni = np.diff(R.row_off), np.diff(R.col_off)
+    expect = np.minimum(np.minimum(np.ceil(r * ni / n - 1e-12).astype(int), mi), ni)
+    assert np.array_equal(si, expect)
+
+
+@pytest.mark.parametrize("alpha_r", [5, 12, 25])
+def test_single_shot_equals_one_chunk(alpha_r):
+    """Eqs. 2 and 3 as printed (dense M, N) equal the incremental form with one chunk."""
+    m, n = 160, 50
+    rowptr, col, val = _powerlaw(21, m, n, 800)
+    f1 = fastpi.factor(m, n, rowptr, col, val, r=alpha_r, k=0.03, single_shot=True)
+    f2 = fastpi.factor(m, n, rowptr, col, val, r=alpha_r, k=0.03)
+    np.testing.assert_allclose(f2.S, f1.S, rtol=1e-12, atol=1e-13 * f1.S[0])
+    Y = workloads.labels_dense(m, 6, 2, np.random.default_rng(0))
+    Z1, Z2 = fastpi.apply(f1, Y), fastpi.apply(f2, Y)
+    assert np.linalg.norm(Z1 - Z2) <= 1e-10 * np.linalg.norm(Z1)
+
+
+@pytest.mark.parametrize("chunks", [(None, None), (8, 4)])
+def test_eckart_young_and_orthonormality(chunks):
+    m, n = 200, 60
+    rowptr, col, val = _powerlaw(31, m, n, 900)
+    A = _dense(m, n, rowptr, col, val)
+    r = 15
+    f = fastpi.factor(m, n, rowptr, col, val, r=r, k=0.03, chunk_row=chunks[0], chunk_col=chunks[1])
+    sv = np.linalg.svd(A, compute_uv=False)
+    err = np.linalg.norm(A - (f.U * f.S) @ f.V.T)
+    assert err >= np.sqrt(np.sum(sv[r:] ** 2)) * (1 - 1e-12)
+    assert f.S.size == r
+    assert np.all(np.diff(f.S) <= 1e-14 * f.S[0])
+    np.testing.assert_allclose(f.U.T @ f.U, np.eye(r), atol=1e-12)
+    np.testing.assert_allclose(f.V.T @ f.V, np.eye(r), atol=1e-12)
+
+
+def test_dependent_hub_rows_are_dropped():
+    """Duplicate and all-zero border rows give a rank-deficient residual; the
+    factorization is still exact at alpha = 1 (the dropped directions carry nothing)."""
+    m, n = 60, 20
+    rowptr, col, val = _powerlaw(41, m, n, 250)
+    A = _dense(m, n, rowptr, col, val)
+    hub = np.argmax((A != 0).sum(1))
+    A = np.vstack([A, A[hub], A[hub], np.zeros((1, n))])
+    rowptr, col, val = _csr(A)
+    f = fastpi.factor(A.shape[0], n, rowptr, col, val, r=n, k=0.05, chunk_row=2, chunk_col=2)
+    assert np.linalg.norm(A - (f.U * f.S) @ f.V.T) <= 1e-12 * np.linalg.norm(A)
+    sv = np.linalg.svd(A, compute_uv=False)
+    np.testing.assert_allclose(f.S[:sv.size], sv, atol=1e-12 * sv[0])
+
+
+def test_small_workload_residual_close_to_optimal():
+    """On the 2000 x 500 workload the FastPI residual is no better than the
+    unrestricted least-squares optimum (Application 1: Z = A^+ Y minimises
+    |AZ - Y|_F) and within 1% of the residual of the exact rank-r truncated
+    SVD (Section 4.2 reports FastPI's accuracy as near-optimal)."""
+    w = workloads.make("small")
+    m, n, r, k = w["m"], w["n"], w["cfg"].r, w["cfg"].k
+    f = fastpi.factor(m, n, w["rowptr"], w["col"], w["val"], r=r, k=k)
+    A = _dense(m, n, w["rowptr"], w["col"], w["val"])
+    Z = fastpi.apply(f, w["Y"])
+    res = np.linalg.norm(A @ Z - w["Y"])
+    res_r = np.linalg.norm(A @ pinv.dense_solve(A, w["Y"], r) - w["Y"])
+    res_full = np.linalg.norm(A @ np.linalg.lstsq(A, w["Y"], rcond=None)[0] - w["Y"])
+    assert res_full <= res * (1 + 1e-12)
+    assert abs(res - res_r) <= 0.01 * res_r
