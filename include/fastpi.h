@@ -1,0 +1,165 @@
+/*
+ * fastpi.h -- C ABI of libfastpi, a single-GPU (sm_103a) implementation of
+ * FastPI: approximate Moore-Penrose pseudoinverse of a sparse feature matrix by
+ * hub-and-spoke reordering and incremental low-rank SVD (Jung and Sael,
+ * "Fast and Accurate Pseudoinverse with Sparse Matrix Reordering and
+ * Incremental Approach").
+ *
+ * Conventions (all entry points):
+ *   - Every call returns a fastpi_status and never aborts the process.  On an
+ *     error, fastpi_last_error(h) returns a human-readable message.
+ *   - Dense matrices are ROW-MAJOR with an explicit leading dimension (the
+ *     distance in elements between consecutive rows, >= the row length).
+ *   - "device" pointers are CUDA device (or managed) addresses on the device
+ *     that was current when fastpi_create ran; "host" pointers are ordinary
+ *     host memory.  Each argument below says which one it takes.
+ *   - The library owns every allocation it makes; the caller keeps ownership of
+ *     its inputs (they are copied) and of its output buffers.
+ *   - Work is issued on the CUDA stream given to fastpi_create.  Calls that
+ *     return host-visible results synchronise that stream (never the device).
+ *   - Indices are 0-based.  "new" positions refer to the reordered matrix of
+ *     Algorithm 2; "original" to the caller's row / column numbering.
+ */
+#ifndef FASTPI_H
+#define FASTPI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fastpi_ctx* fastpi_t;
+
+typedef enum {
+  FASTPI_OK = 0,
+  FASTPI_ERR_ARG = 1,            /* invalid argument (null handle, bad size, k outside (0,1), ...) */
+  FASTPI_ERR_CSR = 2,            /* malformed CSR: rowptr not monotone, column out of range,
+                                    unsorted or duplicate columns in a row */
+  FASTPI_ERR_OOM = 3,            /* device allocation failed */
+  FASTPI_ERR_CUDA = 4,           /* a CUDA runtime call failed */
+  FASTPI_ERR_NO_CONVERGENCE = 5, /* an iteration cap was reached on the device (Jacobi sweeps,
+                                    union-find retries, a bounded device-wide barrier) */
+  FASTPI_ERR_STATE = 6           /* call out of order (e.g. a getter before fastpi_factor) */
+} fastpi_status;
+
+typedef enum {
+  FASTPI_FP64 = 0,        /* every floating-point step in FP64 */
+  FASTPI_MIXED_TF32 = 1   /* FP32 storage; dense products on TF32 tensor cores with FP32
+                             accumulation; Gram Cholesky and singular values in FP64 */
+} fastpi_precision;
+
+/* Summary of the last factorization (host struct filled by fastpi_get_info). */
+typedef struct {
+  int64_t m, n, nnz;
+  int64_t m1, n1, m2, n2;    /* A11 is m1 x n1; hubs are the trailing m2 rows / n2 columns */
+  int64_t num_blocks;        /* B: diagonal blocks of A11, including empty ones */
+  int64_t iterations;        /* T: iterations of the reordering loop */
+  int64_t S;                 /* columns kept by the block SVD (sum of s_i) */
+  int64_t s_row;             /* rank after the row update */
+  int64_t rank;              /* r' = rank after the column update */
+  int64_t chunk_row, chunk_col;        /* border rows / columns appended per incremental step */
+  int64_t row_chunks, col_chunks;      /* number of incremental steps of each phase */
+  int64_t dropped_directions;          /* residual directions dropped as dependent */
+  int64_t jacobi_sweeps_max;           /* most sweeps any Jacobi SVD needed */
+  double min_trunc_gap;      /* min over truncations of (sigma_keep_last - sigma_drop_first)/sigma_1 */
+  double ms_reorder, ms_block_svd, ms_row_update, ms_col_update, ms_finalize;  /* stage times */
+  int precision;
+} fastpi_info;
+
+/*
+ * fastpi_create -- upload a sparse feature matrix A (m x n, CSR) and build the
+ * handle.  A is the feature matrix of Application 1 (instances = rows,
+ * features = columns); its bipartite network is Definition 1.
+ *   rowptr: int64[m+1], monotone, rowptr[0] = 0, rowptr[m] = nnz
+ *   colind: int32[nnz], strictly increasing within each row, in [0, n)
+ *   val:    float64[nnz]
+ *   ptrs_on_device: 0 -> the three arrays are host pointers; 1 -> device pointers.
+ *   cuda_stream: a cudaStream_t (NULL = legacy default stream) used by every
+ *   later call on this handle.
+ * The arrays are validated (FASTPI_ERR_CSR on failure) and copied; the caller
+ * may free them on return.  *out is set to NULL on any error.
+ */
+fastpi_status fastpi_create(fastpi_t* out, int64_t m, int64_t n, int64_t nnz,
+                            const int64_t* rowptr, const int32_t* colind, const double* val,
+                            int ptrs_on_device, void* cuda_stream);
+
+/*
+ * fastpi_factor -- Algorithm 1, lines 1-4: reorder A by Algorithm 2 (hub ratio
+ * k in (0,1)), SVD of the block-diagonal A11 (Eq. 1, per-block rank
+ * s_i = min(ceil(alpha n_1i), m_1i, n_1i)), row incremental update with A21
+ * (Eq. 2, rank s = min(ceil(alpha n1), S + m2, n1)) and column incremental
+ * update with T = [A12; A22] (Eq. 3, rank r' = min(r, m, s + n2)), where the
+ * target rank ratio is alpha = r / n (Table 1).
+ *   r:     target rank, 1 <= r.
+ *   k:     hub selection ratio, 0 < k < 1.
+ *   prec:  FASTPI_FP64 or FASTPI_MIXED_TF32.
+ *   chunk_row, chunk_col: border rows of A21 / columns of T appended per
+ *          incremental step (0 = library default, 256; >= the border size gives
+ *          the single-shot form of Eqs. 2 and 3).  Each step truncates to the
+ *          phase's target rank.
+ * Re-factoring a handle replaces the previous factors.
+ */
+fastpi_status fastpi_factor(fastpi_t h, int64_t r, double k, fastpi_precision prec,
+                            int64_t chunk_row, int64_t chunk_col);
+
+/*
+ * fastpi_apply -- Problem 1 / Application 1: Z = V Sigma^+ U^T Y for a dense
+ * label matrix.  Sigma^+_ii = 1/sigma_i if sigma_i > tau, else 0, with
+ * tau = max(m, n) * 2^-52 * sigma_1.
+ *   Y: device float64, m x L row-major (ldy >= L), rows in ORIGINAL order.
+ *   Z: device float64, n x L row-major (ldz >= L), rows in ORIGINAL order; overwritten.
+ * FASTPI_ERR_STATE before a successful fastpi_factor.
+ */
+fastpi_status fastpi_apply(fastpi_t h, const double* Y, int64_t L, int64_t ldy,
+                           double* Z, int64_t ldz);
+
+/* fastpi_apply_host -- as fastpi_apply, with Y and Z in HOST memory; the
+ * host<->device copies run on the handle's stream and the call returns when Z
+ * is written. */
+fastpi_status fastpi_apply_host(fastpi_t h, const double* Y, int64_t L, int64_t ldy,
+                                double* Z, int64_t ldz);
+
+/*
+ * fastpi_apply_csr -- as fastpi_apply for a sparse label matrix Y (m x L, CSR,
+ * device pointers: yrowptr int64[m+1], ycol int32[nnz_y] in [0, L), yval
+ * float64[nnz_y]).  Z: device float64 n x L row-major.
+ */
+fastpi_status fastpi_apply_csr(fastpi_t h, int64_t L, int64_t nnz_y, const int64_t* yrowptr,
+                               const int32_t* ycol, const double* yval, double* Z, int64_t ldz);
+
+/* fastpi_residual -- ||A Z - Y||_F in FP64 (Application 1's objective).
+ * Y: device m x L (ldy), Z: device n x L (ldz), both rows in ORIGINAL order.
+ * *out: host double. */
+fastpi_status fastpi_residual(fastpi_t h, const double* Y, int64_t L, int64_t ldy,
+                              const double* Z, int64_t ldz, double* out);
+
+/* Getters (valid after fastpi_factor; FASTPI_ERR_STATE before). */
+fastpi_status fastpi_get_rank(fastpi_t h, int64_t* r_out);            /* host int64 */
+fastpi_status fastpi_get_S(fastpi_t h, double* S);                    /* host float64[r'], descending */
+/* U: device float64 m x r' row-major (ldu >= r'), rows in ORIGINAL order. */
+fastpi_status fastpi_get_U(fastpi_t h, double* U, int64_t ldu);
+/* V: device float64 n x r' row-major (ldv >= r'), rows in ORIGINAL order. */
+fastpi_status fastpi_get_V(fastpi_t h, double* V, int64_t ldv);
+/* Reordering of Algorithm 2 (host arrays): row_order[new] = original row,
+ * col_order[new] = original column; m2 / n2 hub counts (the trailing rows /
+ * columns).  Any output pointer may be NULL. */
+fastpi_status fastpi_get_perm(fastpi_t h, int32_t* row_order, int32_t* col_order,
+                              int64_t* m2, int64_t* n2);
+/* Diagonal blocks of A11 (host arrays of B+1 entries): block b covers new rows
+ * [row_off[b], row_off[b+1]) and new columns [col_off[b], col_off[b+1]).
+ * Pass NULL offsets to query *B only. */
+fastpi_status fastpi_get_blocks(fastpi_t h, int64_t* B, int64_t* row_off, int64_t* col_off);
+fastpi_status fastpi_get_info(fastpi_t h, fastpi_info* info);          /* host struct */
+
+/* Message of the last failed call on h (or of the last failed fastpi_create
+ * when h is NULL).  Never NULL; valid until the next call on h. */
+const char* fastpi_last_error(fastpi_t h);
+
+/* Release every device and host resource of h (NULL is a no-op). */
+void fastpi_destroy(fastpi_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FASTPI_H */

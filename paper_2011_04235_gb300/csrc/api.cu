@@ -1,0 +1,270 @@
+// C ABI of libfastpi (declared in include/fastpi.h).  Every entry point
+// converts internal errors into a status code and a message.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "dense.cuh"
+#include "factor.cuh"
+
+using namespace fastpi;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+fastpi_status handle_error(fastpi_t h, const Error& e) {
+  if (h)
+    h->last_error = e.msg;
+  else
+    g_create_error = e.msg;
+  return e.status;
+}
+
+#define API_BEGIN try {
+#define API_END(h)                                        \
+  }                                                       \
+  catch (const Error& e) {                                \
+    return handle_error(h, e);                            \
+  }                                                       \
+  catch (const std::exception& e) {                       \
+    return handle_error(h, Error{FASTPI_ERR_CUDA, e.what()}); \
+  }                                                       \
+  return FASTPI_OK;
+
+void require(bool ok, fastpi_status s, const char* msg) {
+  if (!ok) fail(s, msg);
+}
+
+void require_factored(fastpi_t h) { require(h->factored && h->fac, FASTPI_ERR_STATE, "call fastpi_factor first"); }
+
+void use_device(fastpi_t h) { CK(cudaSetDevice(h->device)); }
+
+}  // namespace
+
+extern "C" {
+
+fastpi_status fastpi_create(fastpi_t* out, int64_t m, int64_t n, int64_t nnz, const int64_t* rowptr,
+                            const int32_t* colind, const double* val, int ptrs_on_device, void* cuda_stream) {
+  if (out) *out = nullptr;
+  fastpi_ctx* h = nullptr;
+  try {
+    require(out != nullptr, FASTPI_ERR_ARG, "out is NULL");
+    require(m >= 1 && n >= 1 && nnz >= 0, FASTPI_ERR_ARG, "need m >= 1, n >= 1, nnz >= 0");
+    require(m + n < (int64_t(1) << 31) - 1, FASTPI_ERR_ARG, "m + n must fit in int32");
+    require(nnz <= int64_t(m) * int64_t(n), FASTPI_ERR_ARG, "nnz exceeds m * n");
+    require(nnz < (int64_t(1) << 31) - 1, FASTPI_ERR_ARG, "nnz must fit in int32");
+    require(rowptr && (nnz == 0 || (colind && val)), FASTPI_ERR_ARG, "null CSR array");
+    h = new fastpi_ctx();
+    CK(cudaGetDevice(&h->device));
+    CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    {
+      // keep freed stream-ordered memory in the pool between calls
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, h->device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+      }
+      (void)cudaGetLastError();
+    }
+    h->m = m;
+    h->n = n;
+    h->nnz = nnz;
+    cudaStream_t st = h->stream;
+    h->rowptr = DArr<int64_t>(m + 1, st);
+    h->col = DArr<int32_t>(nnz, st);
+    h->val = DArr<double>(nnz, st);
+    h->dstatus = DArr<unsigned>(1, st);
+    cudaMemcpyKind kind = ptrs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(h->rowptr.get(), rowptr, size_t(m + 1) * 8, kind, st));
+    if (nnz > 0) {
+      CK(cudaMemcpyAsync(h->col.get(), colind, size_t(nnz) * 4, kind, st));
+      CK(cudaMemcpyAsync(h->val.get(), val, size_t(nnz) * 8, kind, st));
+    }
+    validate_csr(h);
+    build_csc(h);
+    *out = h;
+    return FASTPI_OK;
+  } catch (const Error& e) {
+    g_create_error = e.msg;
+    delete h;
+    return e.status;
+  } catch (const std::exception& e) {
+    g_create_error = e.what();
+    delete h;
+    return FASTPI_ERR_CUDA;
+  }
+}
+
+fastpi_status fastpi_factor(fastpi_t h, int64_t r, double k, fastpi_precision prec, int64_t chunk_row,
+                            int64_t chunk_col) {
+  if (!h) return FASTPI_ERR_ARG;
+  API_BEGIN
+  use_device(h);
+  require(r >= 1, FASTPI_ERR_ARG, "target rank r must be >= 1");
+  require(k > 0.0 && k < 1.0 && std::isfinite(k), FASTPI_ERR_ARG, "hub ratio k must lie in (0, 1)");
+  require(prec == FASTPI_FP64 || prec == FASTPI_MIXED_TF32, FASTPI_ERR_ARG, "unknown precision");
+  require(chunk_row >= 0 && chunk_col >= 0, FASTPI_ERR_ARG, "chunk sizes must be >= 0");
+  h->factored = false;
+  fastpi::factor(h, r, k, prec, chunk_row, chunk_col);
+  API_END(h)
+}
+
+fastpi_status fastpi_apply(fastpi_t h, const double* Y, int64_t L, int64_t ldy, double* Z, int64_t ldz) {
+  if (!h) return FASTPI_ERR_ARG;
+  API_BEGIN
+  use_device(h);
+  require_factored(h);
+  require(L >= 0 && ldy >= L && ldz >= L, FASTPI_ERR_ARG, "need L >= 0, ldy >= L, ldz >= L");
+  require(L == 0 || (Y && Z), FASTPI_ERR_ARG, "null Y or Z");
+  apply_dense(h, Y, L, ldy, Z, ldz);
+  API_END(h)
+}
+
+fastpi_status fastpi_apply_host(fastpi_t h, const double* Y, int64_t L, int64_t ldy, double* Z, int64_t ldz) {
+  if (!h) return FASTPI_ERR_ARG;
+  API_BEGIN
+  use_device(h);
+  require_factored(h);
+  require(L >= 0 && ldy >= L && ldz >= L, FASTPI_ERR_ARG, "need L >= 0, ldy >= L, ldz >= L");
+  require(L == 0 || (Y && Z), FASTPI_ERR_ARG, "null Y or Z");
+  if (L == 0) return FASTPI_OK;
+  cudaStream_t st = h->stream;
+  DArr<double> dY(h->m * L, st), dZ(h->n * L, st);
+  CK(cudaMemcpy2DAsync(dY.get(), size_t(L) * 8, Y, size_t(ldy) * 8, size_t(L) * 8, size_t(h->m),
+                       cudaMemcpyHostToDevice, st));
+  apply_dense(h, dY.get(), L, L, dZ.get(), L);
+  CK(cudaMemcpy2DAsync(Z, size_t(ldz) * 8, dZ.get(), size_t(L) * 8, size_t(L) * 8, size_t(h->n),
+                       cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  API_END(h)
+}
+
+fastpi_status fastpi_apply_csr(fastpi_t h, int64_t L, int64_t nnz_y, const int64_t* yrowptr, const int32_t* ycol,
+                               const double* yval, double* Z, int64_t ldz) {
+  if (!h) return FASTPI_ERR_ARG;
+  API_BEGIN
+  use_device(h);
+  require_factored(h);
+  require(L >= 0 && ldz >= L && nnz_y >= 0, FASTPI_ERR_ARG, "need L >= 0, ldz >= L, nnz_y >= 0");
+  require(L == 0 || (yrowptr && Z && (nnz_y == 0 || (ycol && yval))), FASTPI_ERR_ARG, "null pointer");
+  apply_csr(h, L, nnz_y, yrowptr, ycol, yval, Z, ldz);
+  API_END(h)
+}
+
+fastpi_status fastpi_residual(fastpi_t h, const double* Y, int64_t L, int64_t ldy, const double* Z, int64_t ldz,
+                              double* out) {
+  if (!h) return FASTPI_ERR_ARG;
+  API_BEGIN
+  use_device(h);
+  require(out != nullptr, FASTPI_ERR_ARG, "out is NULL");
+  require(L >= 0 && ldy >= L && ldz >= L, FASTPI_ERR_ARG, "need L >= 0, ldy >= L, ldz >= L");
+  *out = residual(h, Y, L, ldy, Z, ldz);
+  API_END(h)
+}
+
+fastpi_status fastpi_get_rank(fastpi_t h, int64_t* r_out) {
+  if (!h) return FASTPI_ERR_ARG;
+  API_BEGIN
+  require_factored(h);
+  require(r_out != nullptr, FASTPI_ERR_ARG, "r_out is NULL");
+  *r_out = h->fac->rank;
+  API_END(h)
+}
+
+fastpi_status fastpi_get_S(fastpi_t h, double* S) {
+  if (!h) return FASTPI_ERR_ARG;
+  API_BEGIN
+  require_factored(h);
+  require(S != nullptr || h->fac->rank == 0, FASTPI_ERR_ARG, "S is NULL");
+  if (h->fac->rank > 0) std::memcpy(S, h->fac->S.data(), size_t(h->fac->rank) * 8);
+  API_END(h)
+}
+
+static void get_factor(fastpi_t h, bool isU, double* out, int64_t ld) {
+  Factors& F = *h->fac;
+  const int64_t rows = isU ? F.m : F.n, r = F.rank, ldr = r > 0 ? r : 1;
+  require(ld >= r, FASTPI_ERR_ARG, "leading dimension smaller than the rank");
+  require(out != nullptr || r == 0, FASTPI_ERR_ARG, "output is NULL");
+  if (r == 0) return;
+  cudaStream_t st = h->stream;
+  if (F.prec == FASTPI_FP64)
+    copy2d<double, double>(st, rows, r, isU ? F.U64.get() : F.V64.get(), ldr, out, ld);
+  else
+    copy2d<double, float>(st, rows, r, isU ? F.U32.get() : F.V32.get(), ldr, out, ld);
+  CK(cudaStreamSynchronize(st));
+}
+
+fastpi_status fastpi_get_U(fastpi_t h, double* U, int64_t ldu) {
+  if (!h) return FASTPI_ERR_ARG;
+  API_BEGIN
+  use_device(h);
+  require_factored(h);
+  get_factor(h, true, U, ldu);
+  API_END(h)
+}
+
+fastpi_status fastpi_get_V(fastpi_t h, double* V, int64_t ldv) {
+  if (!h) return FASTPI_ERR_ARG;
+  API_BEGIN
+  use_device(h);
+  require_factored(h);
+  get_factor(h, false, V, ldv);
+  API_END(h)
+}
+
+fastpi_status fastpi_get_perm(fastpi_t h, int32_t* row_order, int32_t* col_order, int64_t* m2, int64_t* n2) {
+  if (!h) return FASTPI_ERR_ARG;
+  API_BEGIN
+  use_device(h);
+  require_factored(h);
+  const Reordering& R = h->fac->R;
+  cudaStream_t st = h->stream;
+  if (row_order) CK(cudaMemcpyAsync(row_order, R.row_order.get(), size_t(R.m) * 4, cudaMemcpyDeviceToHost, st));
+  if (col_order) CK(cudaMemcpyAsync(col_order, R.col_order.get(), size_t(R.n) * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (m2) *m2 = R.m - R.m1;
+  if (n2) *n2 = R.n - R.n1;
+  API_END(h)
+}
+
+fastpi_status fastpi_get_blocks(fastpi_t h, int64_t* B, int64_t* row_off, int64_t* col_off) {
+  if (!h) return FASTPI_ERR_ARG;
+  API_BEGIN
+  require_factored(h);
+  const Reordering& R = h->fac->R;
+  if (B) *B = R.num_blocks;
+  if (row_off) std::memcpy(row_off, R.row_off.data(), R.row_off.size() * 8);
+  if (col_off) std::memcpy(col_off, R.col_off.data(), R.col_off.size() * 8);
+  API_END(h)
+}
+
+fastpi_status fastpi_get_info(fastpi_t h, fastpi_info* info) {
+  if (!h) return FASTPI_ERR_ARG;
+  API_BEGIN
+  require_factored(h);
+  require(info != nullptr, FASTPI_ERR_ARG, "info is NULL");
+  *info = h->info;
+  API_END(h)
+}
+
+const char* fastpi_last_error(fastpi_t h) {
+  if (!h) return g_create_error.c_str();
+  return h->last_error.c_str();
+}
+
+void fastpi_destroy(fastpi_t h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->stream);
+  delete h->fac;
+  h->fac = nullptr;
+  cudaStream_t st = h->stream;
+  delete h;
+  cudaStreamSynchronize(st);
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Internal declarations shared by the libfastpi translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fastpi.h"
+
+namespace fastpi {
+
+// ---------------------------------------------------------------- errors
+struct Error {
+  fastpi_status status;
+  std::string msg;
+};
+
+[[noreturn]] void fail(fastpi_status s, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what, const char* file, int line);
+#define CK(x) ::fastpi::check_cuda((x), #x, __FILE__, __LINE__)
+#define CK_LAUNCH() ::fastpi::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+
+// Device-side status bits (a word in device memory, read at sync points).
+enum : unsigned {
+  ST_BARRIER_TIMEOUT = 1u,   // a bounded device-wide barrier gave up
+  ST_UF_RETRY_CAP = 2u,      // union-find hooking exceeded its retry cap
+  ST_JACOBI_SWEEPS = 4u,     // a Jacobi SVD hit its sweep cap
+  ST_BAD_INDEX = 8u          // an index check failed inside a kernel
+};
+
+// ---------------------------------------------------------------- memory
+// Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync on the owner's
+// stream).  Move-only.
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t st = nullptr;
+  DBuf() = default;
+  DBuf(size_t nbytes, cudaStream_t s);
+  ~DBuf();
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept { *this = static_cast<DBuf&&>(o); }
+  DBuf& operator=(DBuf&& o) noexcept;
+  void reset();
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+template <typename T>
+struct DArr {
+  DBuf b;
+  int64_t n = 0;
+  DArr() = default;
+  DArr(int64_t count, cudaStream_t s) : b(size_t(count > 0 ? count : 1) * sizeof(T), s), n(count) {}
+  T* get() const { return b.as<T>(); }
+  operator T*() const { return get(); }
+};
+
+// ---------------------------------------------------------------- context
+struct Factors;   // defined in factor.cu
+
+}  // namespace fastpi
+
+struct fastpi_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  int64_t m = 0, n = 0, nnz = 0;
+  // A in CSR (device) and its CSC transpose (rows ascending within a column)
+  fastpi::DArr<int64_t> rowptr, colptr;
+  fastpi::DArr<int32_t> col, csc_row;
+  fastpi::DArr<double> val, csc_val;
+  fastpi::DArr<unsigned> dstatus;   // device status word
+  // results
+  bool factored = false;
+  fastpi::Factors* fac = nullptr;
+  fastpi_info info{};
+  std::string last_error;
+};
+
+namespace fastpi {
+
+// ---------------------------------------------------------------- primitives
+// Exclusive prefix sum of n values (out may alias in).  Returns nothing; the
+// total is out[n-1] + in[n-1] (callers that need it pass n+1 with a trailing 0).
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);
+void exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t st);
+
+// Stable LSD radix sort of (key, value) pairs by the low `bits` bits of key.
+// keys/vals are sorted in place (scratch buffers allocated internally).
+void radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits, cudaStream_t st);
+
+// Number of bits needed to represent values in [0, maxval].
+int bits_for(uint64_t maxval);
+
+// Copy device->host of a small POD value / array on the stream and wait.
+void d2h_sync(void* dst, const void* src, size_t bytes, cudaStream_t st);
+
+int ceil_div_i(int64_t a, int64_t b);
+
+}  // namespace fastpi

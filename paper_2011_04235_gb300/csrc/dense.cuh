@@ -1,0 +1,38 @@
+// Dense linear-algebra kernels used by the incremental SVD updates.
+// All matrices are row-major with a leading dimension unless stated.
+#pragma once
+
+#include "common.cuh"
+
+namespace fastpi {
+
+// C (M x N) = alpha * op(A) * op(B) + beta * C.  op(A) is M x K: A is M x K
+// (ta = false) or K x M (ta = true); op(B) is K x N: B is K x N (tb = false)
+// or N x K (tb = true).  beta == 0 never reads C.  Deterministic (split-K
+// partials are reduced in a fixed order).
+template <typename T>
+void gemm(cudaStream_t st, bool ta, bool tb, int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t lda,
+          const T* B, int64_t ldb, T beta, T* C, int64_t ldc);
+
+// Same contract with FP32 storage on the TF32 tensor cores (tcgen05.mma,
+// kind::tf32, FP32 accumulation in tensor memory).  Falls back to nothing:
+// callers use it only when the shape is supported (see gemm_tf32_supported).
+bool gemm_tf32_supported(bool ta, bool tb, int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb,
+                         int64_t ldc, const void* A, const void* B, const void* C);
+void gemm_tf32(cudaStream_t st, bool ta, bool tb, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+               int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc);
+
+// dst[i*ldd + j] = (T)src[i*lds + j] for a rows x cols block.
+template <typename Td, typename Ts>
+void copy2d(cudaStream_t st, int64_t rows, int64_t cols, const Ts* src, int64_t lds, Td* dst, int64_t ldd);
+
+// Gather rows: dst[i, :] = src[idx[i], :] (rows x cols).
+template <typename Td, typename Ts>
+void gather_rows(cudaStream_t st, int64_t rows, int64_t cols, const int32_t* idx, const Ts* src, int64_t lds,
+                 Td* dst, int64_t ldd);
+
+// Set a rows x cols block to zero / the identity (row-major, ld).
+template <typename T> void set_zero(cudaStream_t st, int64_t rows, int64_t cols, T* a, int64_t ld);
+template <typename T> void set_identity(cudaStream_t st, int64_t rows, int64_t cols, T* a, int64_t ld);
+
+}  // namespace fastpi

@@ -1,0 +1,950 @@
+// Algorithm 1 on the device: reorder (Algorithm 2) -> SVD of the A11 blocks
+// (Eq. 1) -> row incremental update with A21 (Eq. 2) -> column incremental
+// update with T = [A12; A22] (Eq. 3); plus the pseudoinverse apply of
+// Problem 1 / Application 1 and the residual of Application 1.
+//
+// Both incremental updates are the same operation on a thin SVD
+// X = Uc diag(sigma) W^T (Uc: p x k orthonormal, W: q x k): append c sparse
+// columns D and keep `target` triplets.  The row update (Eq. 2) runs it on the
+// transpose [V1 Sigma1, A21^T] (Uc = V1, the appended columns are rows of A21,
+// W gives U_row = bdiag(U1, I) W); the column update (Eq. 3) runs it on
+// [U_row Sigma_row, T] (Uc = U_row, W gives V = [[V_row W_top], [W_bot]]).
+// One append step (the incremental SVD the paper cites for Eqs. 2 and 3):
+//   P = Uc^T D (sparse x dense) ; R = D - Uc P ; second pass P2 = Uc^T R,
+//   R -= Uc P2, P += P2 ; CholeskyQR2 of R with dependent directions dropped
+//   (R = Q R_R, zero rows of R_R / zero columns of Q for dropped directions) ;
+//   core K = [[diag(sigma), P], [0, R_R]] ; K = Ut diag(s) Vt^T (Jacobi) ;
+//   keep kk = min(target, k + rank) ; Uc <- [Uc, Q] Ut[:, :kk] ;
+//   W <- [[W, 0], [0, I_c]] Vt[:, :kk].
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include "dense.cuh"
+#include "factor.cuh"
+#include "jacobi.cuh"
+
+namespace fastpi {
+namespace {
+
+constexpr double DROP_TOL_FP64 = 1e-7;    // relative to the largest appended column norm
+constexpr double DROP_TOL_MIXED = 1e-3;   // FP32 residuals: rounding floor near 1e-4
+constexpr double DROP_ABS_PASS2 = 0.25;   // second CholeskyQR pass: kept columns have norm ~1
+constexpr int64_t DEFAULT_CHUNK = 256;    // border rows / columns per append step when the caller passes 0
+
+inline unsigned g1(int64_t n, int bs = 256) { return n > 0 ? unsigned((n + bs - 1) / bs) : 1u; }
+
+struct BlkDesc {
+  int64_t m_b, n_b, s_b, ro, co, soff, data_off, v_off, u_off, sig_off;
+};
+
+// ----------------------------------------------------------------- blocks (Eq. 1)
+template <typename T>
+__global__ void k_block_out(const BlkDesc* __restrict__ d, const T* __restrict__ data, const T* __restrict__ vbuf,
+                            const double* __restrict__ sig, const int32_t* __restrict__ perm, int64_t S, T* V1,
+                            T* U1, double* Sig1) {
+  const BlkDesc b = d[blockIdx.x];
+  const bool tall = b.m_b >= b.n_b;
+  const int64_t p = tall ? b.m_b : b.n_b, q = tall ? b.n_b : b.m_b;
+  const T* B = data + b.data_off;
+  const T* J = vbuf + b.v_off;
+  for (int64_t t = 0; t < b.s_b; ++t) {
+    const int32_t src = perm[b.sig_off + t];
+    const double s = sig[b.sig_off + t];
+    const T inv = s > 0 ? T(1.0 / s) : T(0);
+    if (threadIdx.x == 0) Sig1[b.soff + t] = s;
+    for (int64_t li = threadIdx.x; li < b.m_b; li += blockDim.x)
+      U1[b.u_off + li * b.s_b + t] = tall ? B[int64_t(src) * p + li] * inv : J[int64_t(src) * q + li];
+    for (int64_t j = threadIdx.x; j < b.n_b; j += blockDim.x)
+      V1[(b.co + j) * S + b.soff + t] = tall ? J[int64_t(src) * q + j] : B[int64_t(src) * p + j] * inv;
+  }
+}
+
+__global__ void k_blk_of_row(const int64_t* off, int64_t B, int32_t* blk_of) {
+  int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  for (int64_t i = off[b]; i < off[b + 1]; ++i) blk_of[i] = int32_t(b);
+}
+
+// U_row = [[U1 W_top], [W_bot]] (Eq. 2): U1 block diagonal, packed per block.
+template <typename T>
+__global__ void k_urow(int64_t m, int64_t m1, int64_t s, int64_t S, const int32_t* __restrict__ blk_of_row,
+                       const BlkDesc* __restrict__ bd, const T* __restrict__ U1, const T* __restrict__ W,
+                       int64_t ldw, T* __restrict__ Urow, int64_t ldo) {
+  const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= m) return;
+  if (i >= m1) {
+    const T* src = W + (S + i - m1) * ldw;
+    for (int64_t j = lane; j < s; j += 32) Urow[i * ldo + j] = src[j];
+    return;
+  }
+  const BlkDesc b = bd[blk_of_row[i]];
+  const int64_t li = i - b.ro;
+  for (int64_t j = lane; j < s; j += 32) {
+    T acc = 0;
+    for (int64_t t = 0; t < b.s_b; ++t) acc = fma(U1[b.u_off + li * b.s_b + t], W[(b.soff + t) * ldw + j], acc);
+    Urow[i * ldo + j] = acc;
+  }
+}
+
+// ----------------------------------------------------------------- append step
+// D (p x c, ld c) <- dense copy of sparse columns [a, a + c); dn[t] = |d_t|^2
+template <typename T>
+__global__ void k_scatter_cols(const int64_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                               const double* __restrict__ val, int64_t a, int64_t c, T* D, double* dn) {
+  const int64_t t = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= c) return;
+  double s = 0;
+  for (int64_t e = ptr[a + t] + lane; e < ptr[a + t + 1]; e += 32) {
+    double v = val[e];
+    D[int64_t(idx[e]) * c + t] = T(v);
+    s += v * v;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) dn[t] = s;
+}
+
+// Pt[t, :] = sum_e val_e * Uc[idx_e, :]  (P^T = D^T Uc for sparse D)
+template <typename T>
+__global__ void k_spmm_t(const int64_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                         const double* __restrict__ val, int64_t a, int64_t k, const T* __restrict__ Uc,
+                         int64_t ldu, T* __restrict__ Pt, int64_t ldp) {
+  const int64_t t = blockIdx.x;
+  const int64_t e0 = ptr[a + t], e1 = ptr[a + t + 1];
+  for (int64_t j = threadIdx.x; j < k; j += blockDim.x) {
+    T acc = 0;
+    for (int64_t e = e0; e < e1; ++e) acc = fma(T(val[e]), Uc[int64_t(idx[e]) * ldu + j], acc);
+    Pt[t * ldp + j] = acc;
+  }
+}
+
+template <typename T>
+__global__ void k_axpy2d(int64_t rows, int64_t cols, const T* X, int64_t ldx, T* Y, int64_t ldy) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= rows * cols) return;
+  int64_t i = t / cols, j = t % cols;
+  Y[i * ldy + j] += X[i * ldx + j];
+}
+
+template <typename Td, typename Ts>
+__global__ void k_convert(int64_t n, const Ts* s, Td* d) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < n) d[t] = Td(s[t]);
+}
+
+// Cholesky of the c x c Gram G (row-major, lower triangle used) in FP64,
+// right-looking, one CTA.  A pivot d_j <= thr marks column j as dependent: its
+// column of L is zero (the direction is dropped).  thr = (tol * max_t dn[t])
+// when dn != null, else tol (absolute).  On exit G holds L (upper part zero),
+// kept[j] in {0,1}, *rank = number kept.
+__global__ void k_chol_drop(double* G, int c, const double* dn, double tol, int32_t* kept, int32_t* rank) {
+  __shared__ double s_thr;
+  __shared__ int s_keep;
+  __shared__ double s_ljj;
+  if (threadIdx.x == 0) {
+    double thr = tol;
+    if (dn) {
+      double mx = 0;
+      for (int t = 0; t < c; ++t) mx = fmax(mx, dn[t]);
+      thr = tol * tol * mx;
+    }
+    s_thr = thr;
+  }
+  __syncthreads();
+  int nk = 0;
+  for (int j = 0; j < c; ++j) {
+    if (threadIdx.x == 0) {
+      double d = G[int64_t(j) * c + j];
+      s_keep = d > s_thr;
+      s_ljj = s_keep ? sqrt(d) : 0.0;
+      G[int64_t(j) * c + j] = s_ljj;
+      kept[j] = s_keep;
+    }
+    __syncthreads();
+    const int keep = s_keep;
+    const double inv = keep ? 1.0 / s_ljj : 0.0;
+    nk += keep;
+    for (int i = j + 1 + threadIdx.x; i < c; i += blockDim.x) G[int64_t(i) * c + j] *= inv;
+    __syncthreads();
+    if (keep) {
+      const int nrem = c - j - 1;
+      for (int64_t e = threadIdx.x; e < int64_t(nrem) * nrem; e += blockDim.x) {
+        int i = j + 1 + int(e / nrem), l = j + 1 + int(e % nrem);
+        if (l <= i) G[int64_t(i) * c + l] -= G[int64_t(i) * c + j] * G[int64_t(l) * c + j];
+      }
+    }
+    __syncthreads();
+  }
+  for (int64_t e = threadIdx.x; e < int64_t(c) * c; e += blockDim.x) {
+    int i = int(e / c), l = int(e % c);
+    if (l > i) G[e] = 0.0;
+  }
+  if (threadIdx.x == 0) *rank = nk;
+}
+
+// Cholesky with diagonal pivoting of the c x c Gram G = R^T R (full symmetric,
+// row-major, FP64), one CTA; the pivot rule (largest remaining diagonal, ties
+// to the lower index) is the one of QR with column pivoting on R.  Step t
+// takes the column piv[t] with the largest Schur-complement diagonal d; when
+// that d <= thr = (tol^2 max_t dn[t]) the remaining columns are dependent and
+// the factorization stops at rank = t.  Output, in ORIGINAL column indexing:
+//   Lo (c x c, row-major): Lo[i, t] = L[i, t] for t < rank (zero beyond), so
+//   that G ~ Lo Lo^T and R = Q1 Lo^T with Q1 = R[:, piv[:rank]] L_pp^-T;
+//   Lp (c x c): the rank x rank triangle L_pp[a, b] = Lo[piv[a], b] (zero
+//   elsewhere); kept[a] = (a < rank); piv[t].
+__global__ void k_pchol(const double* G, int c, const double* dn, double tol, double* Lo, double* Lp,
+                        int32_t* kept, int32_t* piv, int32_t* rank_out) {
+  extern __shared__ double psm[];
+  double* d = psm;                                   // c
+  int* used = reinterpret_cast<int*>(psm + c);       // c
+  __shared__ double s_thr, s_best;
+  __shared__ int s_arg, s_rank;
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  for (int i = threadIdx.x; i < c; i += blockDim.x) {
+    d[i] = G[int64_t(i) * c + i];
+    used[i] = 0;
+    kept[i] = 0;
+    piv[i] = -1;
+  }
+  for (int64_t e = threadIdx.x; e < int64_t(c) * c; e += blockDim.x) {
+    Lo[e] = 0.0;
+    Lp[e] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    double mx = 0;
+    for (int t = 0; t < c; ++t) mx = fmax(mx, dn[t]);
+    s_thr = tol * tol * mx;
+    s_rank = 0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int t = 0; t < c; ++t) {
+    // argmax of d over unused columns (ties: lower index)
+    double bv = -1.0;
+    int bi = c;
+    for (int i = threadIdx.x; i < c; i += blockDim.x)
+      if (!used[i] && (d[i] > bv || (d[i] == bv && i < bi))) {
+        bv = d[i];
+        bi = i;
+      }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      red_v[w] = bv;
+      red_i[w] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double v = red_v[0];
+      int ii = red_i[0];
+      for (int q = 1; q < nw; ++q)
+        if (red_v[q] > v || (red_v[q] == v && red_i[q] < ii)) {
+          v = red_v[q];
+          ii = red_i[q];
+        }
+      s_best = v;
+      s_arg = ii;
+    }
+    __syncthreads();
+    if (!(s_best > s_thr) || s_arg >= c) break;   // every remaining column is dependent
+    const int j = s_arg;
+    const double ljj = sqrt(s_best);
+    if (threadIdx.x == 0) {
+      used[j] = 1;
+      piv[t] = j;
+      kept[t] = 1;
+      Lo[int64_t(j) * c + t] = ljj;
+      s_rank = t + 1;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < c; i += blockDim.x) {
+      if (used[i]) continue;
+      double s = G[int64_t(i) * c + j];
+      for (int q = 0; q < t; ++q) s -= Lo[int64_t(i) * c + q] * Lo[int64_t(j) * c + q];
+      const double lit = s / ljj;
+      Lo[int64_t(i) * c + t] = lit;
+      d[i] -= lit * lit;
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  const int rank = s_rank;
+  for (int64_t e = threadIdx.x; e < int64_t(rank) * rank; e += blockDim.x) {
+    const int a = int(e / rank), b = int(e % rank);
+    if (b <= a) Lp[int64_t(a) * c + b] = Lo[int64_t(piv[a]) * c + b];
+  }
+  if (threadIdx.x == 0) *rank_out = rank;
+}
+
+// Linv_orig[a, piv[b]] = X[a, b] for a, b < rank (zero elsewhere): the map
+// that turns R (p x c) into Q1 = R Linv_orig^T.
+// One CTA.
+__global__ void k_scatter_inv(const double* X, const int32_t* piv, const int32_t* rank_p, int c, double* Lio) {
+  const int rank = *rank_p;
+  for (int64_t e = threadIdx.x; e < int64_t(c) * c; e += blockDim.x) Lio[e] = 0.0;
+  __syncthreads();
+  for (int64_t e = threadIdx.x; e < int64_t(rank) * rank; e += blockDim.x) {
+    const int a = int(e / rank), b = int(e % rank);
+    Lio[int64_t(a) * c + piv[b]] = X[int64_t(a) * c + b];
+  }
+}
+
+// X = inverse of L restricted to the kept indices (zero rows / columns for
+// dropped ones), by forward substitution row by row; one CTA.
+__global__ void k_trinv(const double* L, int c, const int32_t* kept, double* X) {
+  for (int64_t e = threadIdx.x; e < int64_t(c) * c; e += blockDim.x) X[e] = 0.0;
+  __syncthreads();
+  for (int i = 0; i < c; ++i) {
+    if (kept[i]) {
+      const double lii = L[int64_t(i) * c + i];
+      for (int j = threadIdx.x; j <= i; j += blockDim.x) {
+        double s = (i == j) ? 1.0 : 0.0;
+        for (int l = j; l < i; ++l) s -= L[int64_t(i) * c + l] * X[int64_t(l) * c + j];
+        X[int64_t(i) * c + j] = s / lii;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// K ((k + c) x (k + c), COLUMN-major) = [[diag(sig), P], [0, R_R]] with
+// P = Pt^T (Pt: c x k, ld ldp) and R_R = M^T (M: c x c row-major, FP64).
+template <typename T>
+__global__ void k_build_core(int64_t k, int64_t c, const double* __restrict__ sig, const T* __restrict__ Pt,
+                             int64_t ldp, const double* __restrict__ M, T* __restrict__ K) {
+  const int64_t n = k + c;
+  int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= n * n) return;
+  const int64_t col = e / n, row = e % n;
+  T v = 0;
+  if (col < k) {
+    if (row == col) v = T(sig[col]);
+  } else {
+    const int64_t t = col - k;
+    if (row < k)
+      v = Pt[t * ldp + row];
+    else
+      v = T(M[t * c + (row - k)]);
+  }
+  K[e] = v;
+}
+
+// Ut[i, t] = K[:, perm[t]] / sig[t] ; Vt[i, t] = J[i, perm[t]]   (n x kk, ld kk)
+template <typename T>
+__global__ void k_core_vectors(int64_t n, int64_t kk, const T* __restrict__ Kb, const T* __restrict__ J,
+                               const double* __restrict__ sig, const int32_t* __restrict__ perm, T* Ut, T* Vt) {
+  int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= n * kk) return;
+  const int64_t i = e / kk, t = e % kk;
+  const int64_t src = perm[t];
+  const double s = sig[t];
+  Ut[e] = s > 0 ? T(double(Kb[src * n + i]) / s) : T(0);
+  Vt[e] = J[src * n + i];
+}
+
+// Single-CTA descending sort of sig[0..k) (ties: lower index first) -> perm.
+__global__ void k_sort_desc(const double* sig, int k, int nq, int32_t* perm, double* sorted) {
+  extern __shared__ unsigned char sm[];
+  double* key = reinterpret_cast<double*>(sm);
+  int* idx = reinterpret_cast<int*>(key + nq);
+  for (int t = threadIdx.x; t < nq; t += blockDim.x) {
+    key[t] = t < k ? sig[t] : -1.0;
+    idx[t] = t;
+  }
+  __syncthreads();
+  for (int size = 2; size <= nq; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < nq; t += blockDim.x) {
+        int u = t ^ stride;
+        if (u > t) {
+          bool up = (t & size) == 0;
+          double ka = key[t], kb = key[u];
+          int ia = idx[t], ib = idx[u];
+          bool a_first = (ka > kb) || (ka == kb && ia < ib);
+          if (a_first != up) {
+            key[t] = kb;
+            key[u] = ka;
+            idx[t] = ib;
+            idx[u] = ia;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int t = threadIdx.x; t < k; t += blockDim.x) {
+    perm[t] = idx[t];
+    sorted[t] = key[t];
+  }
+}
+
+template <typename T>
+__global__ void k_gather_cols(int64_t rows, int64_t kk, const int32_t* perm, const T* src, int64_t lds, T* dst,
+                              int64_t ldd) {
+  int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= rows * kk) return;
+  int64_t i = e / kk, t = e % kk;
+  dst[i * ldd + t] = src[i * lds + perm[t]];
+}
+
+// ----------------------------------------------------------------- phase
+template <typename T>
+struct Phase {
+  fastpi_ctx* h;
+  cudaStream_t st;
+  int64_t p, kmax, qmax, cmax;
+  DArr<T> Uc[2], W[2];
+  DArr<double> sig[2];
+  int cur = 0;
+  int64_t k = 0, q = 0;
+  double drop_tol;
+  // statistics
+  int64_t steps = 0, dropped = 0;
+  int sweeps_max = 0;
+  double min_gap = INFINITY;
+
+  Phase(fastpi_ctx* hh, int64_t p_, int64_t kmax_, int64_t qmax_, int64_t cmax_, double tol)
+      : h(hh), st(hh->stream), p(p_), kmax(kmax_), qmax(qmax_), cmax(cmax_), drop_tol(tol) {
+    for (int i = 0; i < 2; ++i) {
+      Uc[i] = DArr<T>(p * kmax, st);
+      W[i] = DArr<T>(qmax * kmax, st);
+      sig[i] = DArr<double>(kmax + cmax, st);
+    }
+  }
+  T* U() { return Uc[cur].get(); }
+  T* Wm() { return W[cur].get(); }
+  double* S() { return sig[cur].get(); }
+
+  void append(const SparseCols& sc, int64_t a, int64_t c, int64_t target) {
+    const int64_t n = k + c;
+    T* Ucur = U();
+    DArr<T> D(p * c, st), Pt(c * std::max<int64_t>(k, 1), st), P2t(c * std::max<int64_t>(k, 1), st);
+    DArr<double> dn(c, st);
+    set_zero<T>(st, p, c, D.get(), c);
+    k_scatter_cols<T><<<g1(c * 32), 256, 0, st>>>(sc.ptr, sc.idx, sc.val, a, c, D.get(), dn.get());
+    CK_LAUNCH();
+    const int64_t ldp = std::max<int64_t>(k, 1);
+    if (k > 0) {
+      k_spmm_t<T><<<unsigned(c), 256, 0, st>>>(sc.ptr, sc.idx, sc.val, a, k, Ucur, kmax, Pt.get(), ldp);
+      CK_LAUNCH();
+      // R = D - Uc P ; second projection pass
+      gemm<T>(st, false, true, p, c, k, T(-1), Ucur, kmax, Pt.get(), ldp, T(1), D.get(), c);
+      gemm<T>(st, true, false, c, k, p, T(1), D.get(), c, Ucur, kmax, T(0), P2t.get(), ldp);
+      gemm<T>(st, false, true, p, c, k, T(-1), Ucur, kmax, P2t.get(), ldp, T(1), D.get(), c);
+      k_axpy2d<T><<<g1(c * k), 256, 0, st>>>(c, k, P2t.get(), ldp, Pt.get(), ldp);
+      CK_LAUNCH();
+    }
+    // CholeskyQR2 with dependent directions dropped
+    DArr<T> GT(c * c, st), Q1(p * c, st), Q(p * c, st), LinvT(c * c, st);
+    DArr<double> G(c * c, st), Linv(c * c, st), G2(c * c, st), L2inv(c * c, st), M(c * c, st);
+    DArr<double> Lo(c * c, st), Lp(c * c, st), X(c * c, st);
+    DArr<int32_t> kept(c, st), kept2(c, st), piv(c, st), rk(2, st);
+    auto gram = [&](const T* X, double* Gd) {
+      gemm<T>(st, true, false, c, c, p, T(1), X, c, X, c, T(0), GT.get(), c);
+      if (sizeof(T) == 8) {
+        CK(cudaMemcpyAsync(Gd, GT.get(), size_t(c * c) * 8, cudaMemcpyDeviceToDevice, st));
+      } else {
+        k_convert<double, T><<<g1(c * c), 256, 0, st>>>(c * c, GT.get(), Gd);
+        CK_LAUNCH();
+      }
+    };
+    auto to_T = [&](const double* src, T* dst) {
+      if (sizeof(T) == 8) {
+        CK(cudaMemcpyAsync(dst, src, size_t(c * c) * 8, cudaMemcpyDeviceToDevice, st));
+      } else {
+        k_convert<T, double><<<g1(c * c), 256, 0, st>>>(c * c, src, dst);
+        CK_LAUNCH();
+      }
+    };
+    gram(D.get(), G.get());
+    k_pchol<<<1, 1024, size_t(c) * 12, st>>>(G.get(), int(c), dn.get(), drop_tol, Lo.get(), Lp.get(), kept.get(),
+                                             piv.get(), rk.get());
+    k_trinv<<<1, 512, 0, st>>>(Lp.get(), int(c), kept.get(), X.get());
+    k_scatter_inv<<<1, 1024, 0, st>>>(X.get(), piv.get(), rk.get(), int(c), Linv.get());
+    CK_LAUNCH();
+    to_T(Linv.get(), LinvT.get());
+    gemm<T>(st, false, true, p, c, c, T(1), D.get(), c, LinvT.get(), c, T(0), Q1.get(), c);
+    gram(Q1.get(), G2.get());
+    k_chol_drop<<<1, 1024, 0, st>>>(G2.get(), int(c), nullptr, DROP_ABS_PASS2, kept2.get(), rk.get() + 1);
+    k_trinv<<<1, 512, 0, st>>>(G2.get(), int(c), kept2.get(), L2inv.get());
+    CK_LAUNCH();
+    to_T(L2inv.get(), LinvT.get());
+    gemm<T>(st, false, true, p, c, c, T(1), Q1.get(), c, LinvT.get(), c, T(0), Q.get(), c);
+    // R_R = (Lo L2)^T : M = Lo * L2
+    gemm<double>(st, false, false, c, c, c, 1.0, Lo.get(), c, G2.get(), c, 0.0, M.get(), c);
+    // core SVD
+    DArr<T> K(n * n, st), J(n * n, st);
+    k_build_core<T><<<g1(n * n), 256, 0, st>>>(k, c, S(), Pt.get(), ldp, M.get(), K.get());
+    CK_LAUNCH();
+    DArr<double> jsig(n, st);
+    DArr<int32_t> jperm(n, st);
+    std::vector<JacobiProblem<T>> pr(1);
+    pr[0] = JacobiProblem<T>{K.get(), J.get(), n, n, int(n), int(n)};
+    JacobiStats js = jacobi_svd_batched<T>(h, pr, jsig.get(), jperm.get());
+    sweeps_max = std::max(sweeps_max, js.max_sweeps_used);
+    int32_t rks[2];
+    d2h_sync(rks, rk.get(), 8, st);
+    const int64_t rank = std::min<int64_t>(rks[0], rks[1]);
+    dropped += c - rank;
+    const int64_t kk = std::min<int64_t>(target, k + rank);
+    if (kk > kmax) fail(FASTPI_ERR_ARG, "internal: basis exceeds its capacity");
+    if (kk < n) {
+      double sv[2];
+      CK(cudaMemcpyAsync(sv, jsig.get() + (kk > 0 ? kk - 1 : 0), 16, cudaMemcpyDeviceToHost, st));
+      double s1 = 0;
+      CK(cudaMemcpyAsync(&s1, jsig.get(), 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (kk > 0 && s1 > 0) min_gap = std::min(min_gap, (sv[0] - sv[1]) / s1);
+    }
+    // rotations
+    DArr<T> Ut(n * std::max<int64_t>(kk, 1), st), Vt(n * std::max<int64_t>(kk, 1), st);
+    if (kk > 0) {
+      k_core_vectors<T><<<g1(n * kk), 256, 0, st>>>(n, kk, K.get(), J.get(), jsig.get(), jperm.get(), Ut.get(),
+                                                     Vt.get());
+      CK_LAUNCH();
+    }
+    const int nx = cur ^ 1;
+    T* Unew = Uc[nx].get();
+    T* Wnew = W[nx].get();
+    gemm<T>(st, false, false, p, kk, k, T(1), Ucur, kmax, Ut.get(), kk, T(0), Unew, kmax);
+    gemm<T>(st, false, false, p, kk, c, T(1), Q.get(), c, Ut.get() + k * kk, kk, T(1), Unew, kmax);
+    gemm<T>(st, false, false, q, kk, k, T(1), Wm(), kmax, Vt.get(), kk, T(0), Wnew, kmax);
+    copy2d<T, T>(st, c, kk, Vt.get() + k * kk, kk, Wnew + q * kmax, kmax);
+    CK(cudaMemcpyAsync(sig[nx].get(), jsig.get(), size_t(std::max<int64_t>(kk, 1)) * 8, cudaMemcpyDeviceToDevice,
+                       st));
+    cur = nx;
+    k = kk;
+    q += c;
+    ++steps;
+  }
+
+  // Keep the `target` largest triplets when no append step ran.
+  void truncate(int64_t target) {
+    if (k <= target) return;
+    int nq = 1;
+    while (nq < k) nq <<= 1;
+    if (nq > 16384) fail(FASTPI_ERR_ARG, "truncate: too many columns");
+    DArr<int32_t> perm(k, st);
+    DArr<double> sorted(k, st);
+    size_t smem = size_t(nq) * 12;
+    if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_sort_desc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    k_sort_desc<<<1, 1024, smem, st>>>(S(), int(k), nq, perm.get(), sorted.get());
+    CK_LAUNCH();
+    const int nx = cur ^ 1;
+    k_gather_cols<T><<<g1(p * target), 256, 0, st>>>(p, target, perm.get(), U(), kmax, Uc[nx].get(), kmax);
+    k_gather_cols<T><<<g1(q * target), 256, 0, st>>>(q, target, perm.get(), Wm(), kmax, W[nx].get(), kmax);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(sig[nx].get(), sorted.get(), size_t(target) * 8, cudaMemcpyDeviceToDevice, st));
+    cur = nx;
+    k = target;
+  }
+};
+
+template <typename T>
+void run_phase(Phase<T>& ph, const SparseCols& sc, int64_t chunk, int64_t target) {
+  const int64_t total = sc.ncols;
+  for (int64_t a = 0; a < total; a += chunk) {
+    int64_t c = std::min(chunk, total - a);
+    ph.append(sc, a, c, target);
+  }
+  ph.truncate(target);
+}
+
+struct Timer {
+  cudaStream_t st;
+  cudaEvent_t a, b;
+  explicit Timer(cudaStream_t s) : st(s) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+  void start() { cudaEventRecord(a, st); }
+  double stop() {
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  }
+};
+
+template <typename T>
+void factor_impl(fastpi_ctx* h, Factors& F, int64_t r, double kratio, int64_t chunk_row, int64_t chunk_col) {
+  cudaStream_t st = h->stream;
+  const int64_t m = h->m, n = h->n;
+  fastpi_info& info = h->info;
+  Timer tm(st);
+  // ---- Algorithm 2 + split
+  tm.start();
+  Reordering& R = F.R;
+  run_reorder(h, kratio, R);
+  SparseCols A21, Tc;
+  split_border(h, R, A21, Tc);
+  A11Blocks blk;
+  extract_blocks(h, R, r, blk);
+  info.ms_reorder = tm.stop();
+  const int64_t m1 = R.m1, n1 = R.n1, m2 = m - m1, n2 = n - n1, S = blk.S;
+
+  // ---- Eq. 1: batched SVD of the A11 blocks
+  tm.start();
+  std::vector<BlkDesc> bd(blk.B);
+  std::vector<JacobiProblem<T>> probs;
+  std::vector<int64_t> prob_of;
+  int64_t vtot = 0, utot = 0, sigtot = 0;
+  for (int64_t b = 0; b < blk.B; ++b) {
+    BlkDesc& d = bd[b];
+    d.m_b = blk.m_b[b];
+    d.n_b = blk.n_b[b];
+    d.s_b = blk.s_b[b];
+    d.ro = R.row_off[b];
+    d.co = R.col_off[b];
+    d.soff = blk.s_off[b];
+    d.data_off = blk.data_off[b];
+    d.u_off = utot;
+    utot += d.m_b * d.s_b;
+    if (d.s_b > 0) {
+      int64_t q = std::min(d.m_b, d.n_b);
+      d.v_off = vtot;
+      d.sig_off = sigtot;
+      vtot += q * q;
+      sigtot += q;
+    } else {
+      d.v_off = d.sig_off = 0;
+    }
+  }
+  DArr<T> bdata(std::max<int64_t>(blk.total, 1), st), vbuf(std::max<int64_t>(vtot, 1), st);
+  if (blk.total > 0) {
+    if (sizeof(T) == 8)
+      CK(cudaMemcpyAsync(bdata.get(), blk.data.get(), size_t(blk.total) * 8, cudaMemcpyDeviceToDevice, st));
+    else {
+      k_convert<T, double><<<g1(blk.total), 256, 0, st>>>(blk.total, blk.data.get(), bdata.get());
+      CK_LAUNCH();
+    }
+  }
+  for (int64_t b = 0; b < blk.B; ++b) {
+    const BlkDesc& d = bd[b];
+    if (d.s_b == 0) continue;
+    int64_t p = std::max(d.m_b, d.n_b), q = std::min(d.m_b, d.n_b);
+    probs.push_back(JacobiProblem<T>{bdata.get() + d.data_off, vbuf.get() + d.v_off, p, q, int(p), int(q)});
+  }
+  DArr<double> bsig(std::max<int64_t>(sigtot, 1), st);
+  DArr<int32_t> bperm(std::max<int64_t>(sigtot, 1), st);
+  JacobiStats bjs = jacobi_svd_batched<T>(h, probs, bsig.get(), bperm.get());
+  // Row phase basis: V1 (n1 x S); U1 packed per block; Sigma1
+  const int64_t s_row = std::min<int64_t>({(r * n1 + n - 1) / n, S + m2, n1});
+  const int64_t cr = chunk_row > 0 ? chunk_row : DEFAULT_CHUNK;
+  const int64_t kmax_r = std::max<int64_t>({S, s_row, 1});
+  Phase<T> rowp(h, std::max<int64_t>(n1, 1), kmax_r, S + m2, std::min(cr, std::max<int64_t>(m2, 1)),
+                sizeof(T) == 8 ? DROP_TOL_FP64 : DROP_TOL_MIXED);
+  DArr<T> U1(std::max<int64_t>(utot, 1), st);
+  DArr<BlkDesc> d_bd(std::max<int64_t>(blk.B, 1), st);
+  if (blk.B > 0) CK(cudaMemcpyAsync(d_bd.get(), bd.data(), sizeof(BlkDesc) * blk.B, cudaMemcpyHostToDevice, st));
+  set_zero<T>(st, n1, S, rowp.U(), kmax_r);
+  if (S > 0) {
+    // k_block_out writes V1 with leading dimension S; use a staging buffer then copy
+    DArr<T> V1(n1 * S, st);
+    set_zero<T>(st, n1, S, V1.get(), S);
+    std::vector<BlkDesc> act;
+    for (auto& d : bd)
+      if (d.s_b > 0) act.push_back(d);
+    DArr<BlkDesc> d_act(int64_t(act.size()), st);
+    CK(cudaMemcpyAsync(d_act.get(), act.data(), sizeof(BlkDesc) * act.size(), cudaMemcpyHostToDevice, st));
+    k_block_out<T><<<unsigned(act.size()), 128, 0, st>>>(d_act.get(), bdata.get(), vbuf.get(), bsig.get(),
+                                                         bperm.get(), S, V1.get(), U1.get(), rowp.S());
+    CK_LAUNCH();
+    copy2d<T, T>(st, n1, S, V1.get(), S, rowp.U(), kmax_r);
+  }
+  set_identity<T>(st, S, S, rowp.Wm(), kmax_r);
+  rowp.k = S;
+  rowp.q = S;
+  info.ms_block_svd = tm.stop();
+
+  // ---- Eq. 2: row incremental update with A21
+  tm.start();
+  run_phase(rowp, A21, cr, s_row);
+  // U_row = [[U1 W_top], [W_bot]]  (m x s_row, new row order)
+  DArr<T> Urow(m * std::max<int64_t>(s_row, 1), st);
+  {
+    DArr<int32_t> blk_of_row(std::max<int64_t>(m1, 1), st);
+    DArr<int64_t> d_ro(blk.B + 1, st);
+    CK(cudaMemcpyAsync(d_ro.get(), R.row_off.data(), size_t(blk.B + 1) * 8, cudaMemcpyHostToDevice, st));
+    if (blk.B > 0) {
+      k_blk_of_row<<<g1(blk.B), 256, 0, st>>>(d_ro.get(), blk.B, blk_of_row.get());
+      CK_LAUNCH();
+    }
+    k_urow<T><<<g1(m * 32), 256, 0, st>>>(m, m1, rowp.k, S, blk_of_row.get(), d_bd.get(), U1.get(), rowp.Wm(),
+                                          kmax_r, Urow.get(), std::max<int64_t>(s_row, 1));
+    CK_LAUNCH();
+  }
+  info.ms_row_update = tm.stop();
+
+  // ---- Eq. 3: column incremental update with T
+  tm.start();
+  const int64_t s = rowp.k;
+  const int64_t rr = std::min<int64_t>({r, m, s + n2});
+  const int64_t cc = chunk_col > 0 ? chunk_col : DEFAULT_CHUNK;
+  const int64_t kmax_c = std::max<int64_t>({s, rr, 1});
+  Phase<T> colp(h, m, kmax_c, s + n2, std::min(cc, std::max<int64_t>(n2, 1)),
+                sizeof(T) == 8 ? DROP_TOL_FP64 : DROP_TOL_MIXED);
+  copy2d<T, T>(st, m, s, Urow.get(), std::max<int64_t>(s_row, 1), colp.U(), kmax_c);
+  CK(cudaMemcpyAsync(colp.S(), rowp.S(), size_t(std::max<int64_t>(s, 1)) * 8, cudaMemcpyDeviceToDevice, st));
+  set_identity<T>(st, s, s, colp.Wm(), kmax_c);
+  colp.k = s;
+  colp.q = s;
+  run_phase(colp, Tc, cc, rr);
+  info.ms_col_update = tm.stop();
+
+  // ---- V = [[V_row W_top], [W_bot]]; back to the caller's order
+  tm.start();
+  const int64_t rank = colp.k;
+  DArr<T> Vnew(n * std::max<int64_t>(rank, 1), st);
+  gemm<T>(st, false, false, n1, rank, s, T(1), rowp.U(), kmax_r, colp.Wm(), kmax_c, T(0), Vnew.get(),
+          std::max<int64_t>(rank, 1));
+  copy2d<T, T>(st, n2, rank, colp.Wm() + s * kmax_c, kmax_c, Vnew.get() + n1 * std::max<int64_t>(rank, 1),
+               std::max<int64_t>(rank, 1));
+  const int64_t ldr = std::max<int64_t>(rank, 1);
+  if (sizeof(T) == 8) {
+    F.U64 = DArr<double>(m * ldr, st);
+    F.V64 = DArr<double>(n * ldr, st);
+    gather_rows<double, double>(st, m, rank, R.row_pos, (const double*)colp.U(), kmax_c, F.U64.get(), ldr);
+    gather_rows<double, double>(st, n, rank, R.col_pos, (const double*)Vnew.get(), ldr, F.V64.get(), ldr);
+  } else {
+    F.U32 = DArr<float>(m * ldr, st);
+    F.V32 = DArr<float>(n * ldr, st);
+    gather_rows<float, float>(st, m, rank, R.row_pos, (const float*)colp.U(), kmax_c, F.U32.get(), ldr);
+    gather_rows<float, float>(st, n, rank, R.col_pos, (const float*)Vnew.get(), ldr, F.V32.get(), ldr);
+  }
+  F.S.resize(rank);
+  F.S_d = DArr<double>(ldr, st);
+  if (rank > 0) {
+    CK(cudaMemcpyAsync(F.S_d.get(), colp.S(), size_t(rank) * 8, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(F.S.data(), colp.S(), size_t(rank) * 8, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  info.ms_finalize = tm.stop();
+  F.m = m;
+  F.n = n;
+  F.rank = rank;
+  info.m = m;
+  info.n = n;
+  info.nnz = h->nnz;
+  info.m1 = m1;
+  info.n1 = n1;
+  info.m2 = m2;
+  info.n2 = n2;
+  info.num_blocks = R.num_blocks;
+  info.iterations = R.iterations;
+  info.S = S;
+  info.s_row = s;
+  info.rank = rank;
+  info.chunk_row = cr;
+  info.chunk_col = cc;
+  info.row_chunks = rowp.steps;
+  info.col_chunks = colp.steps;
+  info.dropped_directions = rowp.dropped + colp.dropped;
+  info.jacobi_sweeps_max = std::max({bjs.max_sweeps_used, rowp.sweeps_max, colp.sweeps_max});
+  double g = std::min(rowp.min_gap, colp.min_gap);
+  info.min_trunc_gap = std::isfinite(g) ? g : -1.0;
+}
+
+// ----------------------------------------------------------------- apply
+template <typename T>
+__global__ void k_scale_rows(int64_t rows, int64_t cols, const double* sig, double tau, T* X, int64_t ldx) {
+  int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  int64_t i = e / cols, j = e % cols;
+  double s = sig[i];
+  X[i * ldx + j] = s > tau ? T(double(X[i * ldx + j]) / s) : T(0);
+}
+
+// WtT[l, :] = sum over nonzeros y_il of y_il * U[i, :]   (CSC of Y by label)
+template <typename T>
+__global__ void k_spmm_labels(const int64_t* __restrict__ cptr, const int32_t* __restrict__ rows,
+                              const double* __restrict__ vals, int64_t r, const T* __restrict__ U, int64_t ldu,
+                              T* __restrict__ WtT) {
+  const int64_t l = blockIdx.x;
+  for (int64_t j = threadIdx.x; j < r; j += blockDim.x) {
+    T acc = 0;
+    for (int64_t e = cptr[l]; e < cptr[l + 1]; ++e) acc = fma(T(vals[e]), U[int64_t(rows[e]) * ldu + j], acc);
+    WtT[l * r + j] = acc;
+  }
+}
+
+template <typename T>
+__global__ void k_scale_cols(int64_t rows, int64_t cols, const double* sig, double tau, T* X) {
+  int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  int64_t j = e % cols;
+  double s = sig[j];
+  X[e] = s > tau ? T(double(X[e]) / s) : T(0);
+}
+
+__global__ void k_residual_rows(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                const double* __restrict__ val, int64_t m, int64_t L, const double* __restrict__ Y,
+                                int64_t ldy, const double* __restrict__ Z, int64_t ldz, double* out) {
+  const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= m) return;
+  double acc2 = 0;
+  for (int64_t l = lane; l < L; l += 32) {
+    double s = -Y[i * ldy + l];
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) s = fma(val[e], Z[int64_t(col[e]) * ldz + l], s);
+    acc2 = fma(s, s, acc2);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+  if (lane == 0) out[i] = acc2;
+}
+
+__global__ void k_sum(const double* x, int64_t n, double* out) {
+  __shared__ double ws[32];
+  double s = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += ws[w];
+    *out = t;
+  }
+}
+
+double pinv_tau(const Factors& F) {
+  if (F.S.empty()) return 0.0;
+  double s1 = *std::max_element(F.S.begin(), F.S.end());
+  return double(std::max(F.m, F.n)) * 2.220446049250313e-16 * s1;
+}
+
+}  // namespace
+
+void factor(fastpi_ctx* h, int64_t r, double k, fastpi_precision prec, int64_t chunk_row, int64_t chunk_col) {
+  Factors* F = new Factors();
+  F->prec = int(prec);
+  h->info = fastpi_info{};
+  h->info.precision = int(prec);
+  try {
+    if (prec == FASTPI_FP64)
+      factor_impl<double>(h, *F, r, k, chunk_row, chunk_col);
+    else
+      factor_impl<float>(h, *F, r, k, chunk_row, chunk_col);
+  } catch (...) {
+    delete F;
+    throw;
+  }
+  delete h->fac;
+  h->fac = F;
+  h->factored = true;
+}
+
+void apply_dense(fastpi_ctx* h, const double* Y, int64_t L, int64_t ldy, double* Z, int64_t ldz) {
+  Factors& F = *h->fac;
+  cudaStream_t st = h->stream;
+  const int64_t m = F.m, n = F.n, r = F.rank;
+  const double tau = pinv_tau(F);
+  if (L <= 0) return;
+  if (F.prec == FASTPI_FP64) {
+    DArr<double> Wt(std::max<int64_t>(r, 1) * L, st);
+    gemm<double>(st, true, false, r, L, m, 1.0, F.U64.get(), std::max<int64_t>(r, 1), Y, ldy, 0.0, Wt.get(), L);
+    k_scale_rows<double><<<g1(r * L), 256, 0, st>>>(r, L, F.S_d.get(), tau, Wt.get(), L);
+    CK_LAUNCH();
+    gemm<double>(st, false, false, n, L, r, 1.0, F.V64.get(), std::max<int64_t>(r, 1), Wt.get(), L, 0.0, Z, ldz);
+  } else {
+    DArr<float> Yf(m * L, st), Wt(std::max<int64_t>(r, 1) * L, st), Zf(n * L, st);
+    copy2d<float, double>(st, m, L, Y, ldy, Yf.get(), L);
+    gemm<float>(st, true, false, r, L, m, 1.f, F.U32.get(), std::max<int64_t>(r, 1), Yf.get(), L, 0.f, Wt.get(), L);
+    k_scale_rows<float><<<g1(r * L), 256, 0, st>>>(r, L, F.S_d.get(), tau, Wt.get(), L);
+    CK_LAUNCH();
+    gemm<float>(st, false, false, n, L, r, 1.f, F.V32.get(), std::max<int64_t>(r, 1), Wt.get(), L, 0.f, Zf.get(), L);
+    copy2d<double, float>(st, n, L, Zf.get(), L, Z, ldz);
+  }
+}
+
+void apply_csr(fastpi_ctx* h, int64_t L, int64_t nnz_y, const int64_t* yrowptr, const int32_t* ycol,
+               const double* yval, double* Z, int64_t ldz) {
+  Factors& F = *h->fac;
+  cudaStream_t st = h->stream;
+  const int64_t m = F.m, n = F.n, r = F.rank;
+  const double tau = pinv_tau(F);
+  if (L <= 0) return;
+  // CSC of Y by label: stable radix sort of the nonzeros by label
+  DArr<int64_t> cptr(L + 1, st);
+  DArr<int32_t> crow(std::max<int64_t>(nnz_y, 1), st);
+  DArr<double> cval(std::max<int64_t>(nnz_y, 1), st);
+  {
+    fastpi_ctx tmp_ctx;   // scratch handle to reuse the CSC builder on Y
+    tmp_ctx.stream = st;
+    tmp_ctx.m = m;
+    tmp_ctx.n = L;
+    tmp_ctx.nnz = nnz_y;
+    tmp_ctx.rowptr.n = m + 1;
+    // borrow the caller's arrays without ownership
+    tmp_ctx.rowptr.b.p = const_cast<int64_t*>(yrowptr);
+    tmp_ctx.col.b.p = const_cast<int32_t*>(ycol);
+    tmp_ctx.val.b.p = const_cast<double*>(yval);
+    try {
+      build_csc(&tmp_ctx);
+    } catch (...) {
+      tmp_ctx.rowptr.b.p = nullptr;
+      tmp_ctx.col.b.p = nullptr;
+      tmp_ctx.val.b.p = nullptr;
+      throw;
+    }
+    tmp_ctx.rowptr.b.p = nullptr;
+    tmp_ctx.col.b.p = nullptr;
+    tmp_ctx.val.b.p = nullptr;
+    cptr = static_cast<DArr<int64_t>&&>(tmp_ctx.colptr);
+    crow = static_cast<DArr<int32_t>&&>(tmp_ctx.csc_row);
+    cval = static_cast<DArr<double>&&>(tmp_ctx.csc_val);
+  }
+  const int64_t ldr = std::max<int64_t>(r, 1);
+  if (F.prec == FASTPI_FP64) {
+    DArr<double> WtT(L * ldr, st);
+    k_spmm_labels<double><<<unsigned(L), 256, 0, st>>>(cptr.get(), crow.get(), cval.get(), r, F.U64.get(), ldr,
+                                                       WtT.get());
+    k_scale_cols<double><<<g1(L * r), 256, 0, st>>>(L, r, F.S_d.get(), tau, WtT.get());
+    CK_LAUNCH();
+    gemm<double>(st, false, true, n, L, r, 1.0, F.V64.get(), ldr, WtT.get(), ldr, 0.0, Z, ldz);
+  } else {
+    DArr<float> WtT(L * ldr, st), Zf(n * L, st);
+    k_spmm_labels<float><<<unsigned(L), 256, 0, st>>>(cptr.get(), crow.get(), cval.get(), r, F.U32.get(), ldr,
+                                                      WtT.get());
+    k_scale_cols<float><<<g1(L * r), 256, 0, st>>>(L, r, F.S_d.get(), tau, WtT.get());
+    CK_LAUNCH();
+    gemm<float>(st, false, true, n, L, r, 1.f, F.V32.get(), ldr, WtT.get(), ldr, 0.f, Zf.get(), L);
+    copy2d<double, float>(st, n, L, Zf.get(), L, Z, ldz);
+  }
+}
+
+double residual(fastpi_ctx* h, const double* Y, int64_t L, int64_t ldy, const double* Z, int64_t ldz) {
+  cudaStream_t st = h->stream;
+  const int64_t m = h->m;
+  DArr<double> part(std::max<int64_t>(m, 1), st), tot(1, st);
+  if (m > 0 && L > 0) {
+    k_residual_rows<<<g1(m * 32), 256, 0, st>>>(h->rowptr, h->col, h->val, m, L, Y, ldy, Z, ldz, part.get());
+    CK_LAUNCH();
+  } else {
+    CK(cudaMemsetAsync(part.get(), 0, 8, st));
+  }
+  k_sum<<<1, 1024, 0, st>>>(part.get(), m > 0 && L > 0 ? m : 1, tot.get());
+  CK_LAUNCH();
+  double out = 0;
+  d2h_sync(&out, tot.get(), 8, st);
+  return std::sqrt(out);
+}
+
+}  // namespace fastpi

@@ -1,0 +1,26 @@
+// Factorization state kept in a handle after fastpi_factor.
+#pragma once
+
+#include "internal.cuh"
+
+namespace fastpi {
+
+struct Factors {
+  int prec = 0;
+  int64_t m = 0, n = 0, rank = 0;
+  // U (m x rank) and V (n x rank), row-major, ORIGINAL row order; FP64 mode
+  // fills U64/V64, the mixed mode U32/V32.
+  DArr<double> U64, V64;
+  DArr<float> U32, V32;
+  std::vector<double> S;   // host, descending
+  DArr<double> S_d;        // device copy
+  Reordering R;
+};
+
+void factor(fastpi_ctx* h, int64_t r, double k, fastpi_precision prec, int64_t chunk_row, int64_t chunk_col);
+void apply_dense(fastpi_ctx* h, const double* Y, int64_t L, int64_t ldy, double* Z, int64_t ldz);
+void apply_csr(fastpi_ctx* h, int64_t L, int64_t nnz_y, const int64_t* yrowptr, const int32_t* ycol,
+               const double* yval, double* Z, int64_t ldz);
+double residual(fastpi_ctx* h, const double* Y, int64_t L, int64_t ldy, const double* Z, int64_t ldz);
+
+}  // namespace fastpi

@@ -1,0 +1,455 @@
+// Batched one-sided Jacobi SVD (Hestenes' method) in one persistent
+// cooperative launch.
+//
+// Parallel ordering: a problem with q columns (padded to an even qe) runs
+// sweeps of qe - 1 rounds; round r pairs the columns by the circle method
+// (qe - 1 with r, and (r + s, r - s) mod (qe - 1) for s = 1 .. qe/2 - 1), so the
+// qe/2 pairs of a round are disjoint and a sweep visits every pair once.  All
+// problems advance one round per global step; every pair of every active
+// problem is one warp-sized work item; steps are separated by a device-wide
+// barrier whose spin is bounded (on timeout the kernel records
+// ST_BARRIER_TIMEOUT and returns).
+//
+// Rotation (one pair, warp-wide): alpha = |a_i|^2, beta = |a_j|^2,
+// gamma = a_i . a_j; if |gamma| > tol sqrt(alpha beta):
+//   zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + hypot(1, zeta)),
+//   c = 1 / sqrt(1 + t^2), s = c t,  a_i' = c a_i - s a_j,  a_j' = s a_i + c a_j
+// (the same on the columns of V).  A problem has converged when a whole sweep
+// made no rotation; columns whose squared norm is below a tiny fraction of the
+// problem's squared Frobenius norm are treated as zero (they stem from rank
+// deficiency and are never rotated).
+#include <algorithm>
+#include <cmath>
+
+#include "jacobi.cuh"
+
+namespace fastpi {
+namespace {
+
+template <typename T>
+struct DevProb {
+  T* A;
+  T* V;
+  int64_t lda, ldv;
+  int p, q, qe, R;
+  int64_t pair_off;
+  double tol_abs2;   // squared-norm threshold below which a column counts as zero
+};
+
+struct ProbState {
+  unsigned long long offmax[3];
+  int done;
+  int sweeps;
+};
+
+struct GridBar {
+  unsigned count;
+  unsigned gen;
+  int stop;
+  int done_count;
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Device-wide barrier for a cooperative launch.  The last CTA to arrive
+// decides whether every problem is done (all increments of done_count of the
+// step are complete by then) and publishes that decision with the new
+// generation, so every CTA takes the same exit decision.
+__device__ bool grid_barrier(GridBar* gb, int nprob, unsigned* status) {
+  __shared__ int s_stop;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned gen = ld_acquire(&gb->gen);
+    __threadfence();
+    unsigned arrived = atomicAdd(&gb->count, 1u) + 1u;
+    int stop;
+    if (arrived == gridDim.x) {
+      gb->count = 0;
+      stop = (*(volatile int*)&gb->done_count >= nprob) ? 1 : 0;
+      *(volatile int*)&gb->stop = stop;
+      __threadfence();
+      st_release(&gb->gen, gen + 1u);
+    } else {
+      long long spins = 0;
+      stop = 0;
+      while (ld_acquire(&gb->gen) == gen) {
+        if (++spins > (1ll << 24)) {   // ~1-2 s
+          atomicOr(status, ST_BARRIER_TIMEOUT);
+          stop = 1;
+          break;
+        }
+        __nanosleep(64);
+      }
+      if (!stop) stop = *(volatile int*)&gb->stop;
+    }
+    __threadfence();
+    s_stop = stop;
+  }
+  __syncthreads();
+  return s_stop != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int find_prob(const int64_t* pair_off, int nprob, int64_t w) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (pair_off[mid] <= w)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T>
+__global__ void k_fro2(const DevProb<T>* probs, double* fro2) {
+  const DevProb<T> pr = probs[blockIdx.x];
+  double s = 0;
+  for (int j = 0; j < pr.q; ++j)
+    for (int r = threadIdx.x; r < pr.p; r += blockDim.x) {
+      double x = double(pr.A[int64_t(j) * pr.lda + r]);
+      s += x * x;
+    }
+  s = warp_sum(s);
+  __shared__ double ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += ws[w];
+    fro2[blockIdx.x] = t;
+  }
+}
+
+template <typename T>
+__global__ void k_init_v(const DevProb<T>* probs) {
+  const DevProb<T> pr = probs[blockIdx.y];
+  int64_t n = int64_t(pr.q) * pr.q;
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x) {
+    int64_t c = t / pr.q, r = t % pr.q;
+    pr.V[c * pr.ldv + r] = (r == c) ? T(1) : T(0);
+  }
+}
+
+template <typename T, int MAXV>
+__global__ void __launch_bounds__(256) k_jacobi(const DevProb<T>* __restrict__ probs, const int64_t* __restrict__ pair_off,
+                                                int nprob, int64_t total_pairs, ProbState* state, GridBar* gb,
+                                                int max_sweeps, int64_t max_steps, double tol_rel,
+                                                unsigned* status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t t = 0; t < max_steps; ++t) {
+    for (int64_t w = gw; w < total_pairs; w += nw) {
+      const int b = find_prob(pair_off, nprob, w);
+      const DevProb<T> pr = probs[b];
+      if (*(volatile int*)&state[b].done) continue;
+      const int64_t slot = w - pr.pair_off;
+      const int64_t sweep = t / pr.R;
+      const int rr = int(t % pr.R);
+      if (rr == 0 && sweep > 0) {
+        double prev = __longlong_as_double(
+            (long long)(*(volatile unsigned long long*)&state[b].offmax[(sweep - 1) % 3]));
+        bool conv = prev <= tol_rel;
+        if (conv || sweep >= max_sweeps) {
+          if (slot == 0 && lane == 0) {
+            state[b].done = 1;
+            state[b].sweeps = int(sweep);
+            atomicAdd(&gb->done_count, 1);
+            if (!conv) atomicOr(status, ST_JACOBI_SWEEPS);
+          }
+          continue;
+        }
+        if (slot == 0 && lane == 0) state[b].offmax[(sweep + 1) % 3] = 0ull;
+      }
+      const int qe = pr.qe;
+      int i, j;
+      if (slot == 0) {
+        i = qe - 1;
+        j = rr;
+      } else {
+        i = int((rr + slot) % (qe - 1));
+        j = int((rr - slot + qe - 1) % (qe - 1));
+      }
+      if (i > j) {
+        int tmp = i;
+        i = j;
+        j = tmp;
+      }
+      if (j >= pr.q) continue;   // paired with the padding column
+      T* ai = pr.A + int64_t(i) * pr.lda;
+      T* aj = pr.A + int64_t(j) * pr.lda;
+      T* vi = pr.V + int64_t(i) * pr.ldv;
+      T* vj = pr.V + int64_t(j) * pr.ldv;
+      if (pr.p <= 32 * MAXV && pr.q <= 32 * MAXV) {
+        // register-resident pair: every load of the two columns of A and of V
+        // is issued before the first use, so a round costs one L2 round trip
+        T xa[MAXV], ya[MAXV], xv[MAXV], yv[MAXV];
+#pragma unroll
+        for (int u = 0; u < MAXV; ++u) {
+          const int r = lane + 32 * u;
+          const bool ok = r < pr.p, okv = r < pr.q;
+          xa[u] = ok ? __ldcg(ai + r) : T(0);
+          ya[u] = ok ? __ldcg(aj + r) : T(0);
+          xv[u] = okv ? __ldcg(vi + r) : T(0);
+          yv[u] = okv ? __ldcg(vj + r) : T(0);
+        }
+        T al = 0, be = 0, ga = 0;
+#pragma unroll
+        for (int u = 0; u < MAXV; ++u) {
+          al = fma(xa[u], xa[u], al);
+          be = fma(ya[u], ya[u], be);
+          ga = fma(xa[u], ya[u], ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (double(al) <= pr.tol_abs2 || double(be) <= pr.tol_abs2) continue;
+        const double off = fabs(double(ga)) / (sqrt(double(al)) * sqrt(double(be)));
+        if (lane == 0 && off > 0)
+          atomicMax(&state[b].offmax[sweep % 3], (unsigned long long)__double_as_longlong(off));
+        if (!(off > tol_rel)) continue;
+        const T zeta = (be - al) / (T(2) * ga);
+        const T tt = copysign(T(1), zeta) / (fabs(zeta) + hypot(T(1), zeta));
+        const T c = T(1) / sqrt(T(1) + tt * tt);
+        const T s = c * tt;
+#pragma unroll
+        for (int u = 0; u < MAXV; ++u) {
+          const int r = lane + 32 * u;
+          if (r < pr.p) {
+            __stcg(ai + r, c * xa[u] - s * ya[u]);
+            __stcg(aj + r, s * xa[u] + c * ya[u]);
+          }
+          if (r < pr.q) {
+            __stcg(vi + r, c * xv[u] - s * yv[u]);
+            __stcg(vj + r, s * xv[u] + c * yv[u]);
+          }
+        }
+        continue;
+      }
+      // long columns: two passes over L2, loads unrolled four deep
+      T al = 0, be = 0, ga = 0;
+#pragma unroll 4
+      for (int r = lane; r < pr.p; r += 32) {
+        T x = __ldcg(ai + r), y = __ldcg(aj + r);
+        al = fma(x, x, al);
+        be = fma(y, y, be);
+        ga = fma(x, y, ga);
+      }
+      al = warp_sum(al);
+      be = warp_sum(be);
+      ga = warp_sum(ga);
+      if (double(al) <= pr.tol_abs2 || double(be) <= pr.tol_abs2) continue;
+      double off = fabs(double(ga)) / (sqrt(double(al)) * sqrt(double(be)));
+      if (lane == 0 && off > 0)
+        atomicMax(&state[b].offmax[sweep % 3], (unsigned long long)__double_as_longlong(off));
+      if (!(off > tol_rel)) continue;
+      T zeta = (be - al) / (T(2) * ga);
+      T tt = copysign(T(1), zeta) / (fabs(zeta) + hypot(T(1), zeta));
+      T c = T(1) / sqrt(T(1) + tt * tt);
+      T s = c * tt;
+#pragma unroll 4
+      for (int r = lane; r < pr.p; r += 32) {
+        T x = __ldcg(ai + r), y = __ldcg(aj + r);
+        __stcg(ai + r, c * x - s * y);
+        __stcg(aj + r, s * x + c * y);
+      }
+#pragma unroll 4
+      for (int r = lane; r < pr.q; r += 32) {
+        T x = __ldcg(vi + r), y = __ldcg(vj + r);
+        __stcg(vi + r, c * x - s * y);
+        __stcg(vj + r, s * x + c * y);
+      }
+    }
+    if (grid_barrier(gb, nprob, status)) break;
+  }
+}
+
+// Per problem: sigma_j = |b_j| and a descending sort (ties: lower index first).
+template <typename T>
+__global__ void k_finish(const DevProb<T>* probs, const int64_t* sig_off, double* sig, int32_t* perm, int nq_max) {
+  extern __shared__ unsigned char smem_raw[];
+  const DevProb<T> pr = probs[blockIdx.x];
+  int nq = 1;
+  while (nq < pr.q) nq <<= 1;
+  double* key = reinterpret_cast<double*>(smem_raw);
+  int* idx = reinterpret_cast<int*>(key + nq_max);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int j = w; j < nq; j += nwarp) {
+    double s = 0;
+    if (j < pr.q) {
+      const T* col = pr.A + int64_t(j) * pr.lda;
+      for (int r = lane; r < pr.p; r += 32) {
+        double x = double(__ldcg(col + r));
+        s += x * x;
+      }
+      s = warp_sum(s);
+    }
+    if (lane == 0) {
+      key[j] = j < pr.q ? sqrt(s) : -1.0;
+      idx[j] = j;
+    }
+  }
+  __syncthreads();
+  // bitonic sort: descending key, ascending index on ties
+  for (int size = 2; size <= nq; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < nq; t += blockDim.x) {
+        int u = t ^ stride;
+        if (u > t) {
+          bool up = ((t & size) == 0);
+          double ka = key[t], kb = key[u];
+          int ia = idx[t], ib = idx[u];
+          bool a_first = (ka > kb) || (ka == kb && ia < ib);
+          if (a_first != up) {
+            key[t] = kb;
+            key[u] = ka;
+            idx[t] = ib;
+            idx[u] = ia;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const int64_t o = sig_off[blockIdx.x];
+  for (int t = threadIdx.x; t < pr.q; t += blockDim.x) {
+    sig[o + t] = key[t];
+    perm[o + t] = idx[t];
+  }
+}
+
+template <typename T> struct Eps;
+template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; };
+template <> struct Eps<float> { static constexpr double v = 1.1920928955078125e-07; };
+
+}  // namespace
+
+template <typename T>
+JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& probs, double* sig,
+                               int32_t* perm) {
+  JacobiStats stats;
+  const int nprob = int(probs.size());
+  if (nprob == 0) return stats;
+  cudaStream_t st = h->stream;
+  std::vector<DevProb<T>> dp(nprob);
+  std::vector<int64_t> pair_off(nprob), sig_off(nprob);
+  int64_t pairs = 0, soff = 0;
+  int maxR = 1, maxq = 1, maxp = 1;
+  for (int b = 0; b < nprob; ++b) {
+    const auto& P = probs[b];
+    DevProb<T>& d = dp[b];
+    d.A = P.A;
+    d.V = P.V;
+    d.lda = P.lda;
+    d.ldv = P.ldv;
+    d.p = P.p;
+    d.q = P.q;
+    d.qe = P.q + (P.q & 1);
+    if (d.qe < 2) d.qe = 2;
+    d.R = d.qe - 1;
+    d.pair_off = pairs;
+    d.tol_abs2 = 0;
+    pair_off[b] = pairs;
+    sig_off[b] = soff;
+    pairs += d.qe / 2;
+    soff += P.q;
+    maxR = std::max(maxR, d.R);
+    maxq = std::max(maxq, P.q);
+    maxp = std::max(maxp, P.p);
+  }
+  if (maxq > 8192) fail(FASTPI_ERR_ARG, "Jacobi SVD: more than 8192 columns in one problem");
+  DArr<DevProb<T>> d_probs(nprob, st);
+  DArr<int64_t> d_pair_off(nprob, st), d_sig_off(nprob, st);
+  DArr<double> fro2(nprob, st);
+  CK(cudaMemcpyAsync(d_probs.get(), dp.data(), sizeof(DevProb<T>) * nprob, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_pair_off.get(), pair_off.data(), 8 * nprob, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_sig_off.get(), sig_off.data(), 8 * nprob, cudaMemcpyHostToDevice, st));
+  // absolute column threshold: (q * eps)^2 * |A|_F^2
+  k_fro2<T><<<nprob, 256, 0, st>>>(d_probs, fro2);
+  CK_LAUNCH();
+  std::vector<double> f2(nprob);
+  d2h_sync(f2.data(), fro2.get(), 8 * nprob, st);
+  for (int b = 0; b < nprob; ++b) {
+    double e = double(std::max(dp[b].q, dp[b].p)) * Eps<T>::v;
+    dp[b].tol_abs2 = e * e * f2[b];
+  }
+  CK(cudaMemcpyAsync(d_probs.get(), dp.data(), sizeof(DevProb<T>) * nprob, cudaMemcpyHostToDevice, st));
+  {
+    dim3 g(unsigned(std::min<int64_t>(64, (int64_t(maxq) * maxq + 255) / 256)), unsigned(nprob));
+    k_init_v<T><<<g, 256, 0, st>>>(d_probs);
+    CK_LAUNCH();
+  }
+  DArr<ProbState> state(nprob, st);
+  DArr<GridBar> gb(1, st);
+  CK(cudaMemsetAsync(state.get(), 0, sizeof(ProbState) * nprob, st));
+  CK(cudaMemsetAsync(gb.get(), 0, sizeof(GridBar), st));
+  CK(cudaMemsetAsync(h->dstatus.get(), 0, 4, st));
+
+  const int max_sweeps = sizeof(T) == 8 ? 40 : 30;
+  const double tol_rel = std::sqrt(double(maxp)) * Eps<T>::v;
+  // registers per lane per column: the smallest that holds the longest column
+  const int need = (std::max(maxp, maxq) + 31) / 32;
+  void* kern = (void*)k_jacobi<T, 8>;   // also the kernel for long columns (two-pass path)
+  if (need > 8 && need <= 16) kern = (void*)k_jacobi<T, 16>;
+  if constexpr (sizeof(T) == 4) {
+    if (need > 16 && need <= 32) kern = (void*)k_jacobi<T, 32>;
+  }
+  int occ = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0));
+  if (occ < 1) occ = 1;
+  int64_t want = (pairs + 7) / 8;
+  int64_t cap = int64_t(h->num_sms) * occ;
+  int grid = int(std::max<int64_t>(1, std::min(want, cap)));
+  int64_t max_steps = int64_t(max_sweeps + 2) * maxR + 2;
+  int nprob_arg = nprob;
+  int64_t pairs_arg = pairs;
+  DevProb<T>* a0 = d_probs.get();
+  int64_t* a1 = d_pair_off.get();
+  ProbState* a4 = state.get();
+  GridBar* a5 = gb.get();
+  int a6 = max_sweeps;
+  int64_t a7 = max_steps;
+  double a8 = tol_rel;
+  unsigned* a9 = h->dstatus.get();
+  void* args[] = {&a0, &a1, &nprob_arg, &pairs_arg, &a4, &a5, &a6, &a7, &a8, &a9};
+  CK(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(256), args, 0, st));
+  CK_LAUNCH();
+
+  int nq_max = 1;
+  while (nq_max < maxq) nq_max <<= 1;
+  size_t smem = size_t(nq_max) * (sizeof(double) + sizeof(int));
+  if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_finish<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  k_finish<T><<<nprob, 512, smem, st>>>(d_probs, d_sig_off, sig, perm, nq_max);
+  CK_LAUNCH();
+
+  unsigned stat = 0;
+  d2h_sync(&stat, h->dstatus.get(), 4, st);
+  std::vector<ProbState> hs(nprob);
+  d2h_sync(hs.data(), state.get(), sizeof(ProbState) * nprob, st);
+  for (auto& s : hs) stats.max_sweeps_used = std::max(stats.max_sweeps_used, s.sweeps);
+  if (stat & ST_BARRIER_TIMEOUT) fail(FASTPI_ERR_NO_CONVERGENCE, "Jacobi SVD: device-wide barrier timed out");
+  stats.hit_cap = (stat & ST_JACOBI_SWEEPS) != 0;
+  return stats;
+}
+
+template JacobiStats jacobi_svd_batched<double>(fastpi_ctx*, const std::vector<JacobiProblem<double>>&, double*,
+                                                int32_t*);
+template JacobiStats jacobi_svd_batched<float>(fastpi_ctx*, const std::vector<JacobiProblem<float>>&, double*,
+                                               int32_t*);
+
+}  // namespace fastpi

@@ -1,0 +1,226 @@
+"""Thin ctypes binding of libfastpi (include/fastpi.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Tensors are PyTorch tensors (device memory and streams come from
+PyTorch); the library receives raw pointers and the current CUDA stream.
+Importing this module loads ``libfastpi.so`` from this package directory and
+raises if it is missing (build it with ``python -m paper_2011_04235_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfastpi.so")
+
+FASTPI_FP64 = 0
+FASTPI_MIXED_TF32 = 1
+PRECISIONS = {"fp64": FASTPI_FP64, "mixed": FASTPI_MIXED_TF32, "tf32": FASTPI_MIXED_TF32}
+
+STATUS = {0: "FASTPI_OK", 1: "FASTPI_ERR_ARG", 2: "FASTPI_ERR_CSR", 3: "FASTPI_ERR_OOM", 4: "FASTPI_ERR_CUDA",
+          5: "FASTPI_ERR_NO_CONVERGENCE", 6: "FASTPI_ERR_STATE"}
+
+# every symbol the header declares
+SYMBOLS = ["fastpi_create", "fastpi_factor", "fastpi_apply", "fastpi_apply_host", "fastpi_apply_csr",
+           "fastpi_residual", "fastpi_get_rank", "fastpi_get_S", "fastpi_get_U", "fastpi_get_V",
+           "fastpi_get_perm", "fastpi_get_blocks", "fastpi_get_info", "fastpi_last_error", "fastpi_destroy"]
+
+
+class FastPIError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Info(C.Structure):
+    _fields_ = [(name, C.c_int64) for name in
+                ("m", "n", "nnz", "m1", "n1", "m2", "n2", "num_blocks", "iterations", "S", "s_row", "rank",
+                 "chunk_row", "chunk_col", "row_chunks", "col_chunks", "dropped_directions",
+                 "jacobi_sweeps_max")] + \
+              [("min_trunc_gap", C.c_double), ("ms_reorder", C.c_double), ("ms_block_svd", C.c_double),
+               ("ms_row_update", C.c_double), ("ms_col_update", C.c_double), ("ms_finalize", C.c_double),
+               ("precision", C.c_int)]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_}
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libfastpi.so not built at {path}; run python -m paper_2011_04235_gb300.build")
+    lib = C.CDLL(path)
+    p, i64, i32, dbl, vp = C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_void_p
+    sig = {
+        "fastpi_create": ([C.POINTER(p), i64, i64, i64, vp, vp, vp, i32, vp], i32),
+        "fastpi_factor": ([p, i64, dbl, i32, i64, i64], i32),
+        "fastpi_apply": ([p, vp, i64, i64, vp, i64], i32),
+        "fastpi_apply_host": ([p, vp, i64, i64, vp, i64], i32),
+        "fastpi_apply_csr": ([p, i64, i64, vp, vp, vp, vp, i64], i32),
+        "fastpi_residual": ([p, vp, i64, i64, vp, i64, C.POINTER(dbl)], i32),
+        "fastpi_get_rank": ([p, C.POINTER(i64)], i32),
+        "fastpi_get_S": ([p, vp], i32),
+        "fastpi_get_U": ([p, vp, i64], i32),
+        "fastpi_get_V": ([p, vp, i64], i32),
+        "fastpi_get_perm": ([p, vp, vp, C.POINTER(i64), C.POINTER(i64)], i32),
+        "fastpi_get_blocks": ([p, C.POINTER(i64), vp, vp], i32),
+        "fastpi_get_info": ([p, C.POINTER(Info)], i32),
+        "fastpi_last_error": ([p], C.c_char_p),
+        "fastpi_destroy": ([p], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def _check(st: int, h=None):
+    if st != 0:
+        msg = lib().fastpi_last_error(h)
+        raise FastPIError(st, msg.decode() if msg else "")
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+def _stream_ptr(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+class FastPI:
+    """A factorization handle.  ``A`` is given in CSR (rowptr int64, col int32,
+    val float64), as numpy arrays (host) or CUDA tensors (device)."""
+
+    def __init__(self, m: int, n: int, rowptr, col, val, device="cuda:0", stream=None):
+        self.device = torch.device(device)
+        self.m, self.n = int(m), int(n)
+        on_dev = isinstance(rowptr, torch.Tensor) and rowptr.is_cuda
+        if on_dev:
+            rp = rowptr.to(torch.int64).contiguous()
+            cl = col.to(torch.int32).contiguous()
+            vl = val.to(torch.float64).contiguous()
+            keep = (rp, cl, vl)
+            ptrs = [_ptr(t) for t in keep]
+        else:
+            rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+            cl = np.ascontiguousarray(col, dtype=np.int32)
+            vl = np.ascontiguousarray(val, dtype=np.float64)
+            keep = (rp, cl, vl)
+            ptrs = [a.ctypes.data for a in keep]
+        self.nnz = int(cl.numel() if on_dev else cl.size)
+        self._h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            st = stream if stream is not None else _stream_ptr(self.device)
+            self._stream = st
+            _check(lib().fastpi_create(C.byref(self._h), self.m, self.n, self.nnz, ptrs[0], ptrs[1], ptrs[2],
+                                       1 if on_dev else 0, st))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().fastpi_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def factor(self, r: int, k: float, precision="fp64", chunk_row: int = 0, chunk_col: int = 0):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        with torch.cuda.device(self.device):
+            _check(lib().fastpi_factor(self._h, int(r), float(k), prec, int(chunk_row), int(chunk_col)), self._h)
+        return self
+
+    def apply(self, Y: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        assert Y.is_cuda and Y.dtype == torch.float64 and Y.dim() == 2 and Y.shape[0] == self.m
+        Y = Y if Y.stride(1) == 1 else Y.contiguous()
+        L = Y.shape[1]
+        Z = out if out is not None else torch.empty((self.n, L), dtype=torch.float64, device=Y.device)
+        with torch.cuda.device(self.device):
+            _check(lib().fastpi_apply(self._h, _ptr(Y), L, Y.stride(0), _ptr(Z), Z.stride(0)), self._h)
+        return Z
+
+    def apply_host(self, Y: np.ndarray) -> np.ndarray:
+        Y = np.ascontiguousarray(Y, dtype=np.float64)
+        Z = np.empty((self.n, Y.shape[1]), dtype=np.float64)
+        with torch.cuda.device(self.device):
+            _check(lib().fastpi_apply_host(self._h, Y.ctypes.data, Y.shape[1], Y.shape[1], Z.ctypes.data,
+                                           Z.shape[1]), self._h)
+        return Z
+
+    def apply_csr(self, L: int, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor) -> torch.Tensor:
+        Z = torch.empty((self.n, L), dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            _check(lib().fastpi_apply_csr(self._h, int(L), int(col.numel()), _ptr(rowptr), _ptr(col), _ptr(val),
+                                          _ptr(Z), L), self._h)
+        return Z
+
+    def residual(self, Y: torch.Tensor, Z: torch.Tensor) -> float:
+        out = C.c_double()
+        with torch.cuda.device(self.device):
+            _check(lib().fastpi_residual(self._h, _ptr(Y), Y.shape[1], Y.stride(0), _ptr(Z), Z.stride(0),
+                                         C.byref(out)), self._h)
+        return out.value
+
+    @property
+    def rank(self) -> int:
+        r = C.c_int64()
+        _check(lib().fastpi_get_rank(self._h, C.byref(r)), self._h)
+        return r.value
+
+    def S(self) -> np.ndarray:
+        s = np.empty(self.rank, dtype=np.float64)
+        _check(lib().fastpi_get_S(self._h, s.ctypes.data), self._h)
+        return s
+
+    def U(self) -> torch.Tensor:
+        r = self.rank
+        U = torch.empty((self.m, max(r, 1)), dtype=torch.float64, device=self.device)[:, :r]
+        with torch.cuda.device(self.device):
+            _check(lib().fastpi_get_U(self._h, _ptr(U), U.stride(0)), self._h)
+        return U
+
+    def V(self) -> torch.Tensor:
+        r = self.rank
+        V = torch.empty((self.n, max(r, 1)), dtype=torch.float64, device=self.device)[:, :r]
+        with torch.cuda.device(self.device):
+            _check(lib().fastpi_get_V(self._h, _ptr(V), V.stride(0)), self._h)
+        return V
+
+    def perm(self):
+        ro = np.empty(self.m, dtype=np.int32)
+        co = np.empty(self.n, dtype=np.int32)
+        m2, n2 = C.c_int64(), C.c_int64()
+        with torch.cuda.device(self.device):
+            _check(lib().fastpi_get_perm(self._h, ro.ctypes.data, co.ctypes.data, C.byref(m2), C.byref(n2)),
+                   self._h)
+        return ro, co, m2.value, n2.value
+
+    def blocks(self):
+        B = C.c_int64()
+        _check(lib().fastpi_get_blocks(self._h, C.byref(B), None, None), self._h)
+        ro = np.empty(B.value + 1, dtype=np.int64)
+        co = np.empty(B.value + 1, dtype=np.int64)
+        _check(lib().fastpi_get_blocks(self._h, C.byref(B), ro.ctypes.data, co.ctypes.data), self._h)
+        return ro, co
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(lib().fastpi_get_info(self._h, C.byref(inf)), self._h)
+        return inf.as_dict()

@@ -1,0 +1,38 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads without a
+GPU, and exports every function that include/fastpi.h declares (no compute
+call is made)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "fastpi.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fastpi_[A-Za-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2011_04235_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    names = _declared()
+    assert "fastpi_create" in names and "fastpi_apply" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_binding_lists_every_declared_symbol():
+    from paper_2011_04235_gb300 import fastpi
+    assert sorted(fastpi.SYMBOLS) == _declared()
+    lib = fastpi.lib()
+    for n in fastpi.SYMBOLS:
+        assert hasattr(lib, n)
+
+
+def test_last_error_without_handle():
+    from paper_2011_04235_gb300 import fastpi
+    # a NULL handle is accepted and returns a (possibly empty) message
+    assert isinstance(fastpi.lib().fastpi_last_error(None), bytes)
