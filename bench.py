@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark: FastPI factor + solve (Algorithm 1 + Problem 1) on the seeded
+20000 x 5000 power-law workload (500k nonzeros, r = 500, k = 0.01, Y 20000 x 400).
+
+One step = fastpi_factor + fastpi_apply on one GPU with the matrix and Y
+already resident in HBM.  The headline `value` is the mixed-precision form
+in GFLOP/s of a fixed flop model of the method's shapes (the same count for
+every implementation, so FP64, mixed and the CPU oracle compare directly);
+the FP64 form is timed beside it and both residuals |AZ - Y|_F are reported.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank factors its own copy of the workload
+(replicas: the method does not shard); rank 0 prints one JSON line.
+`--impl reference` times the FP64 CPU oracle (the reference arm) on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "A†Y factor+solve seconds and GFLOP/s at rank r, mixed vs FP64 at same residual"
+WORKLOAD = "medium"
+CHUNK = 256
+
+
+# ----------------------------------------------------------------------------- flop model
+def flop_model(m, n, nnz_a21, nnz_t, m1, n1, m2, n2, row_off, col_off, r, L, chunk):
+    """Flops of FastPI factor + solve from the method's shapes (Algorithm 1 with
+    the chunked updates of Eqs. 2 / 3).  Dense SVD of a p x q matrix (p >= q)
+    with vectors counts 4 p q^2 + 8 q^3.  One append of c columns to a rank-k
+    basis of length p (q rows of coefficients, nnzc nonzeros, kk kept):
+    2 nnzc k (projection) + 6 p k c (residual, second pass) + 8 p c^2
+    (two Gram matrices, two triangular applies) + 12 (k + c)^3 (core SVD)
+    + 2 p (k + c) kk + 2 q k kk (rotations)."""
+    ceil_a = lambda x: (r * x + n - 1) // n
+    mb = np.diff(row_off)
+    nb = np.diff(col_off)
+    sb = np.minimum(np.minimum(ceil_a(nb), mb), nb)
+    p = np.maximum(mb, nb).astype(float)
+    q = np.minimum(mb, nb).astype(float)
+    live = sb > 0
+    F = float(np.sum(4 * p[live] * q[live] ** 2 + 8 * q[live] ** 3))
+    S = int(sb.sum())
+
+    def phase(pdim, k, q0, total, target, nnz_total):
+        nonlocal F
+        qrows = q0
+        for a in range(0, total, chunk):
+            c = min(chunk, total - a)
+            nnzc = nnz_total * c / max(total, 1)
+            kk = min(target, k + c)
+            F += (2 * nnzc * k + 6 * pdim * k * c + 8 * pdim * c * c + 12 * (k + c) ** 3
+                  + 2 * pdim * (k + c) * kk + 2 * qrows * k * kk)
+            k = kk
+            qrows += c
+        return min(k, target)
+
+    s = int(min(ceil_a(n1), S + m2, n1))
+    s = phase(n1, S, S, m2, s, nnz_a21)
+    F += 2.0 * float(np.sum(mb * sb)) * s            # U_row = bdiag(U1, I) W
+    rr = int(min(r, m, s + n2))
+    rr = phase(m, s, s, n2, rr, nnz_t)
+    F += 2.0 * n1 * s * rr                           # V = [[V_row W_top], [W_bot]]
+    F += 2.0 * m * rr * L + 2.0 * n * rr * L         # Z = V Sigma^+ (U^T Y)
+    return F
+
+
+def workload_flops(w, reo_row_order, reo_col_order, row_off, col_off, m1, n1, chunk):
+    m, n, cfg = w["m"], w["n"], w["cfg"]
+    rows = np.repeat(np.arange(m), np.diff(w["rowptr"]))
+    pos_r = np.empty(m, dtype=np.int64)
+    pos_r[reo_row_order] = np.arange(m)
+    pos_c = np.empty(n, dtype=np.int64)
+    pos_c[reo_col_order] = np.arange(n)
+    nr, nc = pos_r[rows], pos_c[w["col"]]
+    nnz_a21 = int(np.count_nonzero((nr >= m1) & (nc < n1)))
+    nnz_t = int(np.count_nonzero(nc >= n1))
+    L = w["Y"].shape[1]
+    return flop_model(m, n, nnz_a21, nnz_t, m1, n1, m - m1, n - n1, np.asarray(row_off), np.asarray(col_off),
+                      cfg.r, L, chunk)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines: list[str] = []
+        self.proc = None
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+def oracle_sample(w, budget_s: float = 60.0):
+    """Time the FP64 CPU oracle, as it stands, on the whole workload: reorder,
+    block SVD, row and column updates with the same chunk schedule, and the
+    apply.  Returns (GFLOP/s under the bench's flop model, seconds,
+    description, BLAS threads)."""
+    from oracle import fastpi as ofp
+
+    cfg = w["cfg"]
+    t0 = time.perf_counter()
+    f = ofp.factor(w["m"], w["n"], w["rowptr"], w["col"], w["val"], cfg.r, cfg.k, chunk_row=CHUNK, chunk_col=CHUNK)
+    ofp.apply(f, w["Y"])
+    secs = time.perf_counter() - t0
+    reo = f.reo
+    F = workload_flops(w, reo.row_order, reo.col_order, reo.row_off, reo.col_off, reo.m1, reo.n1, CHUNK)
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max((d.get("num_threads", 1) for d in threadpool_info()), default=1)
+    except Exception:
+        threads = len(os.sched_getaffinity(0))
+    desc = (f"FP64 oracle (NumPy/SciPy LAPACK) on the whole {cfg.name} workload: reorder, block SVD, "
+            f"row and column updates with chunk {CHUNK}, apply; flops by the bench's flop model")
+    return F / secs / 1e9, secs, desc, threads
+
+
+# ----------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        w = workloads.make(WORKLOAD)
+        vals, secs = [], []
+        desc, threads = "", 1
+        for _ in range(args.steps):
+            g, s, desc, threads = oracle_sample(w, budget_s=20.0)
+            vals.append(g)
+            secs.append(s)
+        v = statistics.mean(vals)
+        out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GFLOP/s", "n_gpus": args.gpus,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(secs),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "config": {"workload": w["cfg"].name, "chunk": CHUNK},
+               "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+                                "sample": desc},
+               "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+
+    import torch
+
+    if not torch.cuda.is_available():
+        print(json.dumps({"impl": "ours", "unavailable": "no CUDA device"}))
+        return
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    from paper_2011_04235_gb300 import build as _build
+    if rank == 0:
+        _build.build()
+    if pg:
+        pg.barrier()
+    from paper_2011_04235_gb300 import fastpi
+
+    w = workloads.make(WORKLOAD)
+    cfg = w["cfg"]
+    m, n = w["m"], w["n"]
+    stream = torch.cuda.current_stream(dev)
+    rp = torch.from_numpy(w["rowptr"]).to(dev)
+    cl = torch.from_numpy(w["col"]).to(dev)
+    vl = torch.from_numpy(w["val"]).to(dev)
+    Yd = torch.from_numpy(w["Y"]).to(dev)
+    Z = torch.empty((n, Yd.shape[1]), dtype=torch.float64, device=dev)
+    h = fastpi.FastPI(m, n, rp, cl, vl, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > 129 MB L2
+
+    def step(prec):
+        h.factor(cfg.r, cfg.k, prec, CHUNK, CHUNK)
+        h.apply(Yd, out=Z)
+
+    def timed(prec, steps, warmup, sampler=None):
+        for _ in range(warmup):
+            flush.fill_(1.0)
+            step(prec)
+        torch.cuda.synchronize(dev)
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize(dev)
+        if sampler:
+            sampler.start()
+        fastpi.reset_counters()
+        times = []
+        for _ in range(steps):
+            flush.fill_(2.0)       # L2 flush between steps, outside the timed window
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(prec)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            times.append(e0.elapsed_time(e1) / 1000.0)
+        cnt = fastpi.counters()
+        clocks = sampler.stop() if sampler else None
+        torch.cuda.synchronize(dev)
+        if pg:
+            pg.barrier()
+        return times, cnt, clocks
+
+    # mixed precision: the headline
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    t_mixed, cnt_mixed, clocks = timed("mixed", args.steps, max(args.warmup, 3), sampler)
+    res_mixed = h.residual(Yd, Z)
+    info = h.info()
+    ro, co, _, _ = h.perm()
+    bro, bco = h.blocks()
+    F = workload_flops(w, ro, co, bro, bco, info["m1"], info["n1"], CHUNK)
+    # FP64 form at the same chunk schedule
+    t64, _, _ = timed("fp64", max(args.fp64_steps, 1), 1)
+    res64 = h.residual(Yd, Z)
+    info64 = h.info()
+
+    sec_mixed = statistics.mean(t_mixed)
+    sec_max = sec_mixed
+    if pg:
+        tt = torch.tensor([sec_mixed], device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        sec_max = float(tt.item())
+    value = world * F / sec_max / 1e9
+
+    # end to end through the C ABI with host buffers (create + factor + apply_host)
+    e2e = None
+    if not args.no_e2e:
+        e_times = []
+        for i in range(2 + args.steps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            hh = fastpi.FastPI(m, n, w["rowptr"], w["col"], w["val"], device=dev)
+            hh.factor(cfg.r, cfg.k, "mixed", CHUNK, CHUNK)
+            Zh = hh.apply_host(w["Y"])
+            t1 = time.perf_counter()
+            hh.close()
+            if i >= 2:
+                e_times.append(t1 - t0)
+        h2d = w["rowptr"].nbytes + w["col"].nbytes + w["val"].nbytes + w["Y"].nbytes
+        d2h = Zh.nbytes
+        e2e = {"value": world * F / statistics.mean(e_times) / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "seconds_per_step": statistics.mean(e_times)}
+
+    # roofline of the dominant kernel (the FP32 Jacobi SVD, ALU-bound)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12        # TFLOP/s: SMs x FP32 lanes x 2 flop x clock
+    jl = max(cnt_mixed["jacobi_launches"], 1)
+    avg_ms = cnt_mixed["jacobi_ms"] / jl
+    achieved = (cnt_mixed["jacobi_flops"] / jl) / (avg_ms / 1000.0) / 1e12 if avg_ms > 0 else 0.0
+    share = cnt_mixed["jacobi_ms"] / 1000.0 / max(sum(t_mixed), 1e-9)
+    roofline = {"kernel": "k_jacobi<float> (batched one-sided Jacobi SVD)", "bound": "alu",
+                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz "
+                                                "(MEASURED_PEAKS.json)", "time_share": share,
+                "avg_launch_ms": avg_ms, "launches_per_step": cnt_mixed["jacobi_launches"] / args.steps}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        g, s, desc, threads = oracle_sample(w, budget_s=20.0)
+        cpu = {"value": g, "unit": "GFLOP/s", "cores": threads, "kind": "oracle", "sample": desc, "seconds": s}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": 1000 * sec_mixed, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": cfg.name, "m": m, "n": n, "nnz": int(w["col"].size), "r": cfg.r, "k": cfg.k,
+                       "L": int(Yd.shape[1]), "chunk": CHUNK, "gamma": cfg.gamma, "seed": 0,
+                       "precision": "mixed: FP32 storage and FP32 SIMT products, FP64 Gram Cholesky, "
+                                    "FP32 Jacobi core SVD",
+                       "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"},
+            "mixed": {"seconds": sec_mixed, "gflops": F / sec_mixed / 1e9, "residual": res_mixed,
+                      "stage_ms": {k: info[k] for k in info if k.startswith("ms_")}},
+            "fp64": {"seconds": statistics.mean(t64), "gflops": F / statistics.mean(t64) / 1e9,
+                     "residual": res64, "stage_ms": {k: info64[k] for k in info64 if k.startswith("ms_")}},
+            "residual_gap_rel": abs(res_mixed - res64) / res64,
+            "speedup_mixed_vs_fp64": statistics.mean(t64) / sec_mixed,
+            "flops_per_step": F,
+            "reorder": {k: info[k] for k in ("m1", "n1", "m2", "n2", "num_blocks", "iterations", "S", "s_row",
+                                               "rank", "row_chunks", "col_chunks", "jacobi_sweeps_max")},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(cnt_mixed["kernel_launches"]),
+            "clocks": clocks,
+        }
+        print(json.dumps(out))
+    h.close()
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -152,6 +152,21 @@ fastpi_status fastpi_get_perm(fastpi_t h, int32_t* row_order, int32_t* col_order
 fastpi_status fastpi_get_blocks(fastpi_t h, int64_t* B, int64_t* row_off, int64_t* col_off);
 fastpi_status fastpi_get_info(fastpi_t h, fastpi_info* info);          /* host struct */
 
+/* Process-wide diagnostic counters (no citation: instrumentation of this
+ * library, not a step of the method).  kernel_launches counts every kernel
+ * this library launched; the jacobi_* fields cover the batched Jacobi SVD
+ * kernel: launches, summed device time from CUDA events recorded on the
+ * launching stream, and algorithmic flops, counted per problem as
+ * sweeps * q(q-1)/2 pair visits * (12 p + 6 q) for a p x q problem. */
+typedef struct {
+  uint64_t kernel_launches;
+  uint64_t jacobi_launches;
+  double jacobi_ms;
+  double jacobi_flops;
+} fastpi_counters;
+fastpi_status fastpi_get_counters(fastpi_counters* out);   /* host struct */
+void fastpi_reset_counters(void);
+
 /* Message of the last failed call on h (or of the last failed fastpi_create
  * when h is NULL).  Never NULL; valid until the next call on h. */
 const char* fastpi_last_error(fastpi_t h);

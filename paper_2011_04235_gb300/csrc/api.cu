@@ -251,6 +251,14 @@ fastpi_status fastpi_get_info(fastpi_t h, fastpi_info* info) {
   API_END(h)
 }
 
+fastpi_status fastpi_get_counters(fastpi_counters* out) {
+  if (!out) return FASTPI_ERR_ARG;
+  read_counters(out);
+  return FASTPI_OK;
+}
+
+void fastpi_reset_counters(void) { reset_counters(); }
+
 const char* fastpi_last_error(fastpi_t h) {
   if (!h) return g_create_error.c_str();
   return h->last_error.c_str();

@@ -19,8 +19,15 @@ struct Error {
 
 [[noreturn]] void fail(fastpi_status s, const std::string& msg);
 void check_cuda(cudaError_t e, const char* what, const char* file, int line);
+// Checks the launch that precedes it and counts it (every kernel launch in
+// this library is followed by exactly one CK_LAUNCH).
+void note_launch(const char* file, int line);
 #define CK(x) ::fastpi::check_cuda((x), #x, __FILE__, __LINE__)
-#define CK_LAUNCH() ::fastpi::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+#define CK_LAUNCH() ::fastpi::note_launch(__FILE__, __LINE__)
+// Adds one event-timed launch of the Jacobi kernel to the process counters.
+void note_jacobi(double ms, double flops);
+void read_counters(fastpi_counters* out);
+void reset_counters();
 
 // Device-side status bits (a word in device memory, read at sync points).
 enum : unsigned {

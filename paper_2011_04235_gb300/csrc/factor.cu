@@ -469,13 +469,16 @@ struct Phase {
     gram(D.get(), G.get());
     k_pchol<<<1, 1024, size_t(c) * 12, st>>>(G.get(), int(c), dn.get(), drop_tol, Lo.get(), Lp.get(), kept.get(),
                                              piv.get(), rk.get());
+    CK_LAUNCH();
     k_trinv<<<1, 512, 0, st>>>(Lp.get(), int(c), kept.get(), X.get());
+    CK_LAUNCH();
     k_scatter_inv<<<1, 1024, 0, st>>>(X.get(), piv.get(), rk.get(), int(c), Linv.get());
     CK_LAUNCH();
     to_T(Linv.get(), LinvT.get());
     gemm<T>(st, false, true, p, c, c, T(1), D.get(), c, LinvT.get(), c, T(0), Q1.get(), c);
     gram(Q1.get(), G2.get());
     k_chol_drop<<<1, 1024, 0, st>>>(G2.get(), int(c), nullptr, DROP_ABS_PASS2, kept2.get(), rk.get() + 1);
+    CK_LAUNCH();
     k_trinv<<<1, 512, 0, st>>>(G2.get(), int(c), kept2.get(), L2inv.get());
     CK_LAUNCH();
     to_T(L2inv.get(), LinvT.get());
@@ -542,6 +545,7 @@ struct Phase {
     CK_LAUNCH();
     const int nx = cur ^ 1;
     k_gather_cols<T><<<g1(p * target), 256, 0, st>>>(p, target, perm.get(), U(), kmax, Uc[nx].get(), kmax);
+    CK_LAUNCH();
     k_gather_cols<T><<<g1(q * target), 256, 0, st>>>(q, target, perm.get(), Wm(), kmax, W[nx].get(), kmax);
     CK_LAUNCH();
     CK(cudaMemcpyAsync(sig[nx].get(), sorted.get(), size_t(target) * 8, cudaMemcpyDeviceToDevice, st));
@@ -916,6 +920,7 @@ void apply_csr(fastpi_ctx* h, int64_t L, int64_t nnz_y, const int64_t* yrowptr, 
     DArr<double> WtT(L * ldr, st);
     k_spmm_labels<double><<<unsigned(L), 256, 0, st>>>(cptr.get(), crow.get(), cval.get(), r, F.U64.get(), ldr,
                                                        WtT.get());
+    CK_LAUNCH();
     k_scale_cols<double><<<g1(L * r), 256, 0, st>>>(L, r, F.S_d.get(), tau, WtT.get());
     CK_LAUNCH();
     gemm<double>(st, false, true, n, L, r, 1.0, F.V64.get(), ldr, WtT.get(), ldr, 0.0, Z, ldz);
@@ -923,6 +928,7 @@ void apply_csr(fastpi_ctx* h, int64_t L, int64_t nnz_y, const int64_t* yrowptr, 
     DArr<float> WtT(L * ldr, st), Zf(n * L, st);
     k_spmm_labels<float><<<unsigned(L), 256, 0, st>>>(cptr.get(), crow.get(), cval.get(), r, F.U32.get(), ldr,
                                                       WtT.get());
+    CK_LAUNCH();
     k_scale_cols<float><<<g1(L * r), 256, 0, st>>>(L, r, F.S_d.get(), tau, WtT.get());
     CK_LAUNCH();
     gemm<float>(st, false, true, n, L, r, 1.f, F.V32.get(), ldr, WtT.get(), ldr, 0.f, Zf.get(), L);

@@ -427,8 +427,13 @@ JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>
   double a8 = tol_rel;
   unsigned* a9 = h->dstatus.get();
   void* args[] = {&a0, &a1, &nprob_arg, &pairs_arg, &a4, &a5, &a6, &a7, &a8, &a9};
+  cudaEvent_t ev0, ev1;
+  CK(cudaEventCreate(&ev0));
+  CK(cudaEventCreate(&ev1));
+  CK(cudaEventRecord(ev0, st));
   CK(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(256), args, 0, st));
   CK_LAUNCH();
+  CK(cudaEventRecord(ev1, st));
 
   int nq_max = 1;
   while (nq_max < maxq) nq_max <<= 1;
@@ -442,6 +447,18 @@ JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>
   std::vector<ProbState> hs(nprob);
   d2h_sync(hs.data(), state.get(), sizeof(ProbState) * nprob, st);
   for (auto& s : hs) stats.max_sweeps_used = std::max(stats.max_sweeps_used, s.sweeps);
+  {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, ev0, ev1));
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    double flops = 0;
+    for (int b = 0; b < nprob; ++b) {
+      const double p = dp[b].p, q = dp[b].q;
+      flops += double(hs[b].sweeps) * (q * (q - 1) / 2) * (12 * p + 6 * q);
+    }
+    note_jacobi(ms, flops);
+  }
   if (stat & ST_BARRIER_TIMEOUT) fail(FASTPI_ERR_NO_CONVERGENCE, "Jacobi SVD: device-wide barrier timed out");
   stats.hit_cap = (stat & ST_JACOBI_SWEEPS) != 0;
   return stats;

@@ -1,13 +1,49 @@
 // Runtime support and data-parallel primitives: errors, stream-ordered
 // buffers, exclusive scans and a stable LSD radix sort.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 
 namespace fastpi {
 
 void fail(fastpi_status s, const std::string& msg) { throw Error{s, msg}; }
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+std::mutex g_prof_mu;
+uint64_t g_jacobi_launches = 0;
+double g_jacobi_ms = 0, g_jacobi_flops = 0;
+}  // namespace
+
+void note_launch(const char* file, int line) {
+  check_cuda(cudaGetLastError(), "kernel launch", file, line);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void note_jacobi(double ms, double flops) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  ++g_jacobi_launches;
+  g_jacobi_ms += ms;
+  g_jacobi_flops += flops;
+}
+
+void read_counters(fastpi_counters* out) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  out->kernel_launches = g_launches.load();
+  out->jacobi_launches = g_jacobi_launches;
+  out->jacobi_ms = g_jacobi_ms;
+  out->jacobi_flops = g_jacobi_flops;
+}
+
+void reset_counters() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_launches.store(0);
+  g_jacobi_launches = 0;
+  g_jacobi_ms = g_jacobi_flops = 0;
+}
 
 void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
   if (e == cudaSuccess) return;

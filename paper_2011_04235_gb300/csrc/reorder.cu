@@ -307,6 +307,7 @@ void build_csc(fastpi_ctx* h) {
   if (nnz > 0) {
     DArr<uint32_t> keys(nnz, st), perm(nnz, st);
     k_keys_from_col<<<nblk(nnz), BS, 0, st>>>(h->col, nnz, keys);
+    CK_LAUNCH();
     k_iota_u32<<<nblk(nnz), BS, 0, st>>>(perm, nnz);
     CK_LAUNCH();
     radix_sort_pairs(keys, perm, nnz, bits_for(uint64_t(n > 0 ? n - 1 : 0)), st);
@@ -365,6 +366,7 @@ void run_reorder(fastpi_ctx* h, double k, Reordering& R) {
     const int64_t n_hub = int64_t(std::ceil(k * double(nF)));
     // degrees in the current graph
     k_deg_rows<<<nblk(m * 32), BS, 0, st>>>(h->rowptr, h->col, act, m, deg);
+    CK_LAUNCH();
     k_deg_cols<<<nblk(n * 32), BS, 0, st>>>(h->colptr, h->csc_row, act, m, n, deg);
     CK_LAUNCH();
     // hubs: instances (key = n - deg so that ascending key = degree descending)
@@ -384,12 +386,18 @@ void run_reorder(fastpi_ctx* h, double k, Reordering& R) {
     }
     // connected components of G'
     k_cc_init<<<nblk(N), BS, 0, st>>>(parent, N);
+    CK_LAUNCH();
     CK(cudaMemsetAsync(cntT.get(), 0, size_t(N) * 4, st));
     CK(cudaMemsetAsync(cntF.get(), 0, size_t(N) * 4, st));
     CK(cudaMemsetAsync(best.get(), 0, 8, st));
-    if (nnz > 0) k_cc_hook<<<nblk(nnz), BS, 0, st>>>(nz_row, h->col, act, m, nnz, parent, h->dstatus);
+    if (nnz > 0) {
+      k_cc_hook<<<nblk(nnz), BS, 0, st>>>(nz_row, h->col, act, m, nnz, parent, h->dstatus);
+      CK_LAUNCH();
+    }
     k_cc_label<<<nblk(N), BS, 0, st>>>(act, N, parent, label, m, cntT, cntF);
+    CK_LAUNCH();
     k_gcc<<<nblk(N), BS, 0, st>>>(act, label, cntT, cntF, N, best);
+    CK_LAUNCH();
     k_summary<<<1, 1, 0, st>>>(best, cntT, cntF, summ);
     CK_LAUNCH();
     int64_t sm[3];
@@ -475,8 +483,14 @@ void run_reorder(fastpi_ctx* h, double k, Reordering& R) {
   R.col_off.resize(nb + 1);
   CK(cudaMemcpyAsync(R.row_off.data(), d_row_off, size_t(nb + 1) * 8, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(R.col_off.data(), d_col_off, size_t(nb + 1) * 8, cudaMemcpyDeviceToHost, st));
-  if (m > 0) k_inverse_perm<<<nblk(m), BS, 0, st>>>(R.row_order, m, R.row_pos);
-  if (n > 0) k_inverse_perm<<<nblk(n), BS, 0, st>>>(R.col_order, n, R.col_pos);
+  if (m > 0) {
+    k_inverse_perm<<<nblk(m), BS, 0, st>>>(R.row_order, m, R.row_pos);
+    CK_LAUNCH();
+  }
+  if (n > 0) {
+    k_inverse_perm<<<nblk(n), BS, 0, st>>>(R.col_order, n, R.col_pos);
+    CK_LAUNCH();
+  }
   CK_LAUNCH();
   CK(cudaStreamSynchronize(st));
 }
@@ -654,6 +668,7 @@ void extract_blocks(fastpi_ctx* h, const Reordering& R, int64_t r, A11Blocks& bl
   CK(cudaMemcpyAsync(d_data_off.get(), blk.data_off.data(), size_t(B) * 8, cudaMemcpyHostToDevice, st));
   DArr<int32_t> blk_of_row(R.m1, st), nz_row(h->nnz, st);
   k_blk_of<<<nblk(B), BS, 0, st>>>(d_row_off, B, blk_of_row);
+  CK_LAUNCH();
   k_row_of_nz<<<nblk(h->m * 32), BS, 0, st>>>(h->rowptr, h->m, nz_row);
   CK_LAUNCH();
   k_blocks_fill<<<nblk(h->nnz), BS, 0, st>>>(nz_row, h->col, h->val, h->nnz, R.row_pos, R.col_pos, R.m1, R.n1,

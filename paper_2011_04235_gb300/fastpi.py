@@ -27,7 +27,8 @@ STATUS = {0: "FASTPI_OK", 1: "FASTPI_ERR_ARG", 2: "FASTPI_ERR_CSR", 3: "FASTPI_E
 # every symbol the header declares
 SYMBOLS = ["fastpi_create", "fastpi_factor", "fastpi_apply", "fastpi_apply_host", "fastpi_apply_csr",
            "fastpi_residual", "fastpi_get_rank", "fastpi_get_S", "fastpi_get_U", "fastpi_get_V",
-           "fastpi_get_perm", "fastpi_get_blocks", "fastpi_get_info", "fastpi_last_error", "fastpi_destroy"]
+           "fastpi_get_perm", "fastpi_get_blocks", "fastpi_get_info", "fastpi_get_counters",
+           "fastpi_reset_counters", "fastpi_last_error", "fastpi_destroy"]
 
 
 class FastPIError(RuntimeError):
@@ -49,6 +50,21 @@ class Info(C.Structure):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
 
 
+class Counters(C.Structure):
+    _fields_ = [("kernel_launches", C.c_uint64), ("jacobi_launches", C.c_uint64), ("jacobi_ms", C.c_double),
+                ("jacobi_flops", C.c_double)]
+
+
+def counters() -> dict:
+    c = Counters()
+    _check(lib().fastpi_get_counters(C.byref(c)))
+    return {f[0]: getattr(c, f[0]) for f in c._fields_}
+
+
+def reset_counters() -> None:
+    lib().fastpi_reset_counters()
+
+
 def load_library(path: str = LIB_PATH) -> C.CDLL:
     if not os.path.exists(path):
         raise ImportError(f"libfastpi.so not built at {path}; run python -m paper_2011_04235_gb300.build")
@@ -68,6 +84,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fastpi_get_perm": ([p, vp, vp, C.POINTER(i64), C.POINTER(i64)], i32),
         "fastpi_get_blocks": ([p, C.POINTER(i64), vp, vp], i32),
         "fastpi_get_info": ([p, C.POINTER(Info)], i32),
+        "fastpi_get_counters": ([C.POINTER(Counters)], i32),
+        "fastpi_reset_counters": ([], None),
         "fastpi_last_error": ([p], C.c_char_p),
         "fastpi_destroy": ([p], None),
     }
