@@ -26,7 +26,8 @@ STATUS = {0: "FASTPI_OK", 1: "FASTPI_ERR_ARG", 2: "FASTPI_ERR_CSR", 3: "FASTPI_E
 
 # every symbol the header declares
 SYMBOLS = ["fastpi_create", "fastpi_factor", "fastpi_apply", "fastpi_apply_host", "fastpi_apply_csr",
-           "fastpi_residual", "fastpi_get_rank", "fastpi_get_S", "fastpi_get_U", "fastpi_get_V",
+           "fastpi_residual", "fastpi_residual_noalloc", "fastpi_get_rank", "fastpi_get_S", "fastpi_get_U",
+           "fastpi_get_V",
            "fastpi_get_perm", "fastpi_get_blocks", "fastpi_get_info", "fastpi_get_counters",
            "fastpi_reset_counters", "fastpi_last_error", "fastpi_destroy"]
 
@@ -65,6 +66,18 @@ def reset_counters() -> None:
     lib().fastpi_reset_counters()
 
 
+def residual_noalloc(m: int, n: int, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,
+                     Y: torch.Tensor, Z: torch.Tensor) -> float:
+    """|A Z - Y|_F through fastpi_residual_noalloc (device tensors, no allocation
+    inside the library; A in CSR: rowptr int64, col int32, val float64)."""
+    out = C.c_double()
+    st = torch.cuda.current_stream(Y.device).cuda_stream
+    with torch.cuda.device(Y.device):
+        _check(lib().fastpi_residual_noalloc(int(m), int(n), _ptr(rowptr), _ptr(col), _ptr(val), _ptr(Y),
+                                             Y.shape[1], Y.stride(0), _ptr(Z), Z.stride(0), C.byref(out), st))
+    return out.value
+
+
 def load_library(path: str = LIB_PATH) -> C.CDLL:
     if not os.path.exists(path):
         raise ImportError(f"libfastpi.so not built at {path}; run python -m paper_2011_04235_gb300.build")
@@ -77,6 +90,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fastpi_apply_host": ([p, vp, i64, i64, vp, i64], i32),
         "fastpi_apply_csr": ([p, i64, i64, vp, vp, vp, vp, i64], i32),
         "fastpi_residual": ([p, vp, i64, i64, vp, i64, C.POINTER(dbl)], i32),
+        "fastpi_residual_noalloc": ([i64, i64, vp, vp, vp, vp, i64, i64, vp, i64, C.POINTER(dbl), vp], i32),
         "fastpi_get_rank": ([p, C.POINTER(i64)], i32),
         "fastpi_get_S": ([p, vp], i32),
         "fastpi_get_U": ([p, vp, i64], i32),
