@@ -14,9 +14,12 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
-template <typename T, bool TA, bool TB>
+// TI: element type of A and B; T: accumulation and output type (products of
+// two FP32 inputs are exact in FP64, so TI = float, T = double accumulates an
+// FP32 product to FP64 accuracy).
+template <typename TI, typename T, bool TA, bool TB>
 __global__ void __launch_bounds__(NT) k_gemm(int64_t M, int64_t N, int64_t K, int64_t kchunk, T alpha,
-                                             const T* __restrict__ A, int64_t lda, const T* __restrict__ B,
+                                             const TI* __restrict__ A, int64_t lda, const TI* __restrict__ B,
                                              int64_t ldb, T beta, T* __restrict__ C, int64_t ldc, T* __restrict__ W) {
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
@@ -44,7 +47,7 @@ __global__ void __launch_bounds__(NT) k_gemm(int64_t M, int64_t N, int64_t K, in
       }
       int64_t gi = m0 + i, gk = k0 + kk;
       T v = T(0);
-      if (gi < M && gk < k_end) v = TA ? A[gk * lda + gi] : A[gi * lda + gk];
+      if (gi < M && gk < k_end) v = T(TA ? A[gk * lda + gi] : A[gi * lda + gk]);
       As[kk][i] = v;
     }
 #pragma unroll
@@ -60,7 +63,7 @@ __global__ void __launch_bounds__(NT) k_gemm(int64_t M, int64_t N, int64_t K, in
       }
       int64_t gj = n0 + j, gk = k0 + kk;
       T v = T(0);
-      if (gj < N && gk < k_end) v = TB ? B[gj * ldb + gk] : B[gk * ldb + gj];
+      if (gj < N && gk < k_end) v = T(TB ? B[gj * ldb + gk] : B[gk * ldb + gj]);
       Bs[kk][j] = v;
     }
     __syncthreads();
@@ -149,9 +152,9 @@ inline unsigned grid1(int64_t n) { return unsigned((n + 255) / 256); }
 
 }  // namespace
 
-template <typename T>
-void gemm(cudaStream_t st, bool ta, bool tb, int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t lda,
-          const T* B, int64_t ldb, T beta, T* C, int64_t ldc) {
+template <typename TI, typename T>
+void gemm_mixed(cudaStream_t st, bool ta, bool tb, int64_t M, int64_t N, int64_t K, T alpha, const TI* A,
+                int64_t lda, const TI* B, int64_t ldb, T beta, T* C, int64_t ldc) {
   if (M <= 0 || N <= 0) return;
   if (K <= 0) {
     // C = beta * C
@@ -181,19 +184,28 @@ void gemm(cudaStream_t st, bool ta, bool tb, int64_t M, int64_t N, int64_t K, T 
   const dim3 grid{unsigned(tn), unsigned(tm), unsigned(splits)};
   T* W = splits > 1 ? work.get() : nullptr;
   if (!ta && !tb)
-    k_gemm<T, false, false><<<grid, NT, 0, st>>>(M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, W);
+    k_gemm<TI, T, false, false><<<grid, NT, 0, st>>>(M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, W);
   else if (ta && !tb)
-    k_gemm<T, true, false><<<grid, NT, 0, st>>>(M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, W);
+    k_gemm<TI, T, true, false><<<grid, NT, 0, st>>>(M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, W);
   else if (!ta && tb)
-    k_gemm<T, false, true><<<grid, NT, 0, st>>>(M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, W);
+    k_gemm<TI, T, false, true><<<grid, NT, 0, st>>>(M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, W);
   else
-    k_gemm<T, true, true><<<grid, NT, 0, st>>>(M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, W);
+    k_gemm<TI, T, true, true><<<grid, NT, 0, st>>>(M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, W);
   CK_LAUNCH();
   if (splits > 1) {
     k_splitk_reduce<T><<<grid1(M * N), 256, 0, st>>>(M, N, splits, W, beta, C, ldc);
     CK_LAUNCH();
   }
 }
+
+template <typename T>
+void gemm(cudaStream_t st, bool ta, bool tb, int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t lda,
+          const T* B, int64_t ldb, T beta, T* C, int64_t ldc) {
+  gemm_mixed<T, T>(st, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+template void gemm_mixed<float, double>(cudaStream_t, bool, bool, int64_t, int64_t, int64_t, double, const float*,
+                                        int64_t, const float*, int64_t, double, double*, int64_t);
 
 template <typename Td, typename Ts>
 void copy2d(cudaStream_t st, int64_t rows, int64_t cols, const Ts* src, int64_t lds, Td* dst, int64_t ldd) {

@@ -14,6 +14,12 @@ template <typename T>
 void gemm(cudaStream_t st, bool ta, bool tb, int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t lda,
           const T* B, int64_t ldb, T beta, T* C, int64_t ldc);
 
+// Same contract with inputs of type TI and accumulation / output in T
+// (instantiated for TI = float, T = double: FP32 data, FP64-accurate sums).
+template <typename TI, typename T>
+void gemm_mixed(cudaStream_t st, bool ta, bool tb, int64_t M, int64_t N, int64_t K, T alpha, const TI* A,
+                int64_t lda, const TI* B, int64_t ldb, T beta, T* C, int64_t ldc);
+
 // Same contract with FP32 storage on the TF32 tensor cores (tcgen05.mma,
 // kind::tf32, FP32 accumulation in tensor memory).  Falls back to nothing:
 // callers use it only when the shape is supported (see gemm_tf32_supported).

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 
 #include "dense.cuh"
 #include "factor.cuh"
@@ -28,7 +29,7 @@ namespace fastpi {
 namespace {
 
 constexpr double DROP_TOL_FP64 = 1e-7;    // relative to the largest appended column norm
-constexpr double DROP_TOL_MIXED = 1e-3;   // FP32 residuals: rounding floor near 1e-4
+constexpr double DROP_TOL_MIXED = 1e-5;   // FP32 residuals: rounding floor near 1e-6
 constexpr double DROP_ABS_PASS2 = 0.25;   // second CholeskyQR pass: kept columns have norm ~1
 constexpr int64_t DEFAULT_CHUNK = 256;    // border rows / columns per append step when the caller passes 0
 
@@ -135,12 +136,13 @@ __global__ void k_convert(int64_t n, const Ts* s, Td* d) {
   if (t < n) d[t] = Td(s[t]);
 }
 
-// Cholesky of the c x c Gram G (row-major, lower triangle used) in FP64,
-// right-looking, one CTA.  A pivot d_j <= thr marks column j as dependent: its
-// column of L is zero (the direction is dropped).  thr = (tol * max_t dn[t])
-// when dn != null, else tol (absolute).  On exit G holds L (upper part zero),
-// kept[j] in {0,1}, *rank = number kept.
-__global__ void k_chol_drop(double* G, int c, const double* dn, double tol, int32_t* kept, int32_t* rank) {
+// Cholesky of the c x c Gram G (row-major, lower triangle used) in the
+// precision of T, right-looking, one CTA.  A pivot d_j <= thr marks column j
+// as dependent: its column of L is zero (the direction is dropped).
+// thr = (tol * max_t dn[t]) when dn != null, else tol (absolute).  On exit G
+// holds L (upper part zero), kept[j] in {0,1}, *rank = number kept.
+template <typename T>
+__global__ void k_chol_drop(T* G, int c, const double* dn, double tol, int32_t* kept, int32_t* rank) {
   __shared__ double s_thr;
   __shared__ int s_keep;
   __shared__ double s_ljj;
@@ -157,15 +159,15 @@ __global__ void k_chol_drop(double* G, int c, const double* dn, double tol, int3
   int nk = 0;
   for (int j = 0; j < c; ++j) {
     if (threadIdx.x == 0) {
-      double d = G[int64_t(j) * c + j];
+      double d = double(G[int64_t(j) * c + j]);
       s_keep = d > s_thr;
       s_ljj = s_keep ? sqrt(d) : 0.0;
-      G[int64_t(j) * c + j] = s_ljj;
+      G[int64_t(j) * c + j] = T(s_ljj);
       kept[j] = s_keep;
     }
     __syncthreads();
     const int keep = s_keep;
-    const double inv = keep ? 1.0 / s_ljj : 0.0;
+    const T inv = keep ? T(1.0 / s_ljj) : T(0);
     nk += keep;
     for (int i = j + 1 + threadIdx.x; i < c; i += blockDim.x) G[int64_t(i) * c + j] *= inv;
     __syncthreads();
@@ -180,8 +182,52 @@ __global__ void k_chol_drop(double* G, int c, const double* dn, double tol, int3
   }
   for (int64_t e = threadIdx.x; e < int64_t(c) * c; e += blockDim.x) {
     int i = int(e / c), l = int(e % c);
-    if (l > i) G[e] = 0.0;
+    if (l > i) G[e] = T(0);
   }
+  if (threadIdx.x == 0) *rank = nk;
+}
+
+// Same result as k_chol_drop, with the lower triangle of G held packed in
+// shared memory for the whole factorization (row i starts at i (i + 1) / 2),
+// so that each of the c sequential steps costs shared-memory latency only.
+template <typename T>
+__global__ void k_chol_drop_smem(T* G, int c, double tol, int32_t* kept, int32_t* rank) {
+  extern __shared__ unsigned char craw[];
+  T* P = reinterpret_cast<T*>(craw);
+  __shared__ int s_keep;
+  __shared__ T s_inv;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = w; i < c; i += nw)
+    for (int l = lane; l <= i; l += 32) P[(int64_t(i) * (i + 1)) / 2 + l] = G[int64_t(i) * c + l];
+  __syncthreads();
+  int nk = 0;
+  for (int j = 0; j < c; ++j) {
+    const int64_t dj = (int64_t(j) * (j + 1)) / 2 + j;
+    if (threadIdx.x == 0) {
+      const double d = double(P[dj]);
+      s_keep = d > tol;
+      const double ljj = s_keep ? sqrt(d) : 0.0;
+      P[dj] = T(ljj);
+      s_inv = s_keep ? T(1.0 / ljj) : T(0);
+      kept[j] = s_keep;
+    }
+    __syncthreads();
+    const int keep = s_keep;
+    nk += keep;
+    const T inv = s_inv;
+    for (int i = j + 1 + threadIdx.x; i < c; i += blockDim.x) P[(int64_t(i) * (i + 1)) / 2 + j] *= inv;
+    __syncthreads();
+    if (keep) {
+      for (int i = j + 1 + w; i < c; i += nw) {
+        const int64_t ri = (int64_t(i) * (i + 1)) / 2;
+        const T lij = P[ri + j];
+        for (int l = j + 1 + lane; l <= i; l += 32) P[ri + l] -= lij * P[(int64_t(l) * (l + 1)) / 2 + j];
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = w; i < c; i += nw)
+    for (int l = lane; l < c; l += 32) G[int64_t(i) * c + l] = l <= i ? P[(int64_t(i) * (i + 1)) / 2 + l] : T(0);
   if (threadIdx.x == 0) *rank = nk;
 }
 
@@ -301,21 +347,27 @@ __global__ void k_scatter_inv(const double* X, const int32_t* piv, const int32_t
 }
 
 // X = inverse of L restricted to the kept indices (zero rows / columns for
-// dropped ones), by forward substitution row by row; one CTA.
-__global__ void k_trinv(const double* L, int c, const int32_t* kept, double* X) {
-  for (int64_t e = threadIdx.x; e < int64_t(c) * c; e += blockDim.x) X[e] = 0.0;
-  __syncthreads();
-  for (int i = 0; i < c; ++i) {
-    if (kept[i]) {
-      const double lii = L[int64_t(i) * c + i];
-      for (int j = threadIdx.x; j <= i; j += blockDim.x) {
-        double s = (i == j) ? 1.0 : 0.0;
-        for (int l = j; l < i; ++l) s -= L[int64_t(i) * c + l] * X[int64_t(l) * c + j];
-        X[int64_t(i) * c + j] = s / lii;
-      }
+// dropped ones).  One warp per column j of X solves L x = e_j by forward
+// substitution; the lanes split each dot product, so the FP64 work of the
+// c columns runs on c different SMs.
+template <typename T>
+__global__ void k_trinv_cols(const T* __restrict__ L, int c, const int32_t* __restrict__ kept, T* X) {
+  extern __shared__ unsigned char xraw[];
+  T* xcol = reinterpret_cast<T*>(xraw);   // c
+  const int j = blockIdx.x, lane = threadIdx.x;
+  for (int i = lane; i < c; i += 32) xcol[i] = T(0);
+  __syncwarp();
+  if (kept[j]) {
+    for (int i = j; i < c; ++i) {
+      T s = T(0);
+      for (int l = j + lane; l < i; l += 32) s = fma(L[int64_t(i) * c + l], xcol[l], s);
+#pragma unroll
+      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) xcol[i] = kept[i] ? (((i == j) ? T(1) : T(0)) - s) / L[int64_t(i) * c + i] : T(0);
+      __syncwarp();
     }
-    __syncthreads();
   }
+  for (int i = lane; i < c; i += 32) X[int64_t(i) * c + j] = xcol[i];
 }
 
 // K ((k + c) x (k + c), COLUMN-major) = [[diag(sig), P], [0, R_R]] with
@@ -408,6 +460,7 @@ struct Phase {
   int cur = 0;
   int64_t k = 0, q = 0;
   double drop_tol;
+  bool use_cluster_svd = true;
   // statistics
   int64_t steps = 0, dropped = 0;
   int sweeps_max = 0;
@@ -449,14 +502,22 @@ struct Phase {
     DArr<double> G(c * c, st), Linv(c * c, st), G2(c * c, st), L2inv(c * c, st), M(c * c, st);
     DArr<double> Lo(c * c, st), Lp(c * c, st), X(c * c, st);
     DArr<int32_t> kept(c, st), kept2(c, st), piv(c, st), rk(2, st);
+    // FP64 Gram of the residual: in the mixed mode from FP32 data with FP64
+    // accumulation (the products are exact), so that its rounding floor sits
+    // far below the drop tolerance
     auto gram = [&](const T* X, double* Gd) {
-      gemm<T>(st, true, false, c, c, p, T(1), X, c, X, c, T(0), GT.get(), c);
-      if (sizeof(T) == 8) {
-        CK(cudaMemcpyAsync(Gd, GT.get(), size_t(c * c) * 8, cudaMemcpyDeviceToDevice, st));
-      } else {
-        k_convert<double, T><<<g1(c * c), 256, 0, st>>>(c * c, GT.get(), Gd);
-        CK_LAUNCH();
-      }
+      if constexpr (sizeof(T) == 8)
+        gemm<double>(st, true, false, c, c, p, 1.0, X, c, X, c, 0.0, Gd, c);
+      else
+        gemm_mixed<float, double>(st, true, false, c, c, p, 1.0, X, c, X, c, 0.0, Gd, c);
+    };
+    auto trinv = [&](auto* L, const int32_t* kp, auto* Xo) {
+      using E = std::remove_pointer_t<decltype(L)>;
+      const size_t sm = size_t(c) * sizeof(E);
+      if (sm > 48 * 1024)
+        CK(cudaFuncSetAttribute(k_trinv_cols<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+      k_trinv_cols<E><<<unsigned(c), 32, sm, st>>>(L, int(c), kp, Xo);
+      CK_LAUNCH();
     };
     auto to_T = [&](const double* src, T* dst) {
       if (sizeof(T) == 8) {
@@ -470,19 +531,32 @@ struct Phase {
     k_pchol<<<1, 1024, size_t(c) * 12, st>>>(G.get(), int(c), dn.get(), drop_tol, Lo.get(), Lp.get(), kept.get(),
                                              piv.get(), rk.get());
     CK_LAUNCH();
-    k_trinv<<<1, 512, 0, st>>>(Lp.get(), int(c), kept.get(), X.get());
-    CK_LAUNCH();
+    trinv(Lp.get(), kept.get(), X.get());
     k_scatter_inv<<<1, 1024, 0, st>>>(X.get(), piv.get(), rk.get(), int(c), Linv.get());
     CK_LAUNCH();
     to_T(Linv.get(), LinvT.get());
     gemm<T>(st, false, true, p, c, c, T(1), D.get(), c, LinvT.get(), c, T(0), Q1.get(), c);
-    gram(Q1.get(), G2.get());
-    k_chol_drop<<<1, 1024, 0, st>>>(G2.get(), int(c), nullptr, DROP_ABS_PASS2, kept2.get(), rk.get() + 1);
-    CK_LAUNCH();
-    k_trinv<<<1, 512, 0, st>>>(G2.get(), int(c), kept2.get(), L2inv.get());
-    CK_LAUNCH();
-    to_T(L2inv.get(), LinvT.get());
+    // second pass: Q1 is orthonormal up to rounding, its Gram ~ I is well
+    // conditioned, so this Cholesky runs in the storage precision
+    gemm<T>(st, true, false, c, c, p, T(1), Q1.get(), c, Q1.get(), c, T(0), GT.get(), c);
+    const size_t packed = size_t(c) * (c + 1) / 2 * sizeof(T);
+    if (packed <= 200 * 1024) {
+      if (packed > 48 * 1024)
+        CK(cudaFuncSetAttribute(k_chol_drop_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(packed)));
+      k_chol_drop_smem<T><<<1, 1024, packed, st>>>(GT.get(), int(c), DROP_ABS_PASS2, kept2.get(), rk.get() + 1);
+      CK_LAUNCH();
+    } else {
+      k_chol_drop<T><<<1, 1024, 0, st>>>(GT.get(), int(c), nullptr, DROP_ABS_PASS2, kept2.get(), rk.get() + 1);
+      CK_LAUNCH();
+    }
+    trinv(GT.get(), kept2.get(), LinvT.get());
     gemm<T>(st, false, true, p, c, c, T(1), Q1.get(), c, LinvT.get(), c, T(0), Q.get(), c);
+    if (sizeof(T) == 8) {
+      CK(cudaMemcpyAsync(G2.get(), GT.get(), size_t(c * c) * 8, cudaMemcpyDeviceToDevice, st));
+    } else {
+      k_convert<double, T><<<g1(c * c), 256, 0, st>>>(c * c, GT.get(), G2.get());
+      CK_LAUNCH();
+    }
     // R_R = (Lo L2)^T : M = Lo * L2
     gemm<double>(st, false, false, c, c, c, 1.0, Lo.get(), c, G2.get(), c, 0.0, M.get(), c);
     // core SVD
@@ -491,24 +565,37 @@ struct Phase {
     CK_LAUNCH();
     DArr<double> jsig(n, st);
     DArr<int32_t> jperm(n, st);
-    std::vector<JacobiProblem<T>> pr(1);
-    pr[0] = JacobiProblem<T>{K.get(), J.get(), n, n, int(n), int(n)};
-    JacobiStats js = jacobi_svd_batched<T>(h, pr, jsig.get(), jperm.get());
+    JacobiStats js;
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+      if (use_cluster_svd) done = jacobi_svd_cluster(h, K.get(), J.get(), int(n), jsig.get(), jperm.get(), &js);
+    }
+    if (!done) {
+      std::vector<JacobiProblem<T>> pr(1);
+      pr[0] = JacobiProblem<T>{K.get(), J.get(), n, n, int(n), int(n)};
+      js = jacobi_svd_batched<T>(h, pr, jsig.get(), jperm.get());
+    }
     sweeps_max = std::max(sweeps_max, js.max_sweeps_used);
     int32_t rks[2];
     d2h_sync(rks, rk.get(), 8, st);
     const int64_t rank = std::min<int64_t>(rks[0], rks[1]);
     dropped += c - rank;
-    const int64_t kk = std::min<int64_t>(target, k + rank);
-    if (kk > kmax) fail(FASTPI_ERR_ARG, "internal: basis exceeds its capacity");
-    if (kk < n) {
-      double sv[2];
-      CK(cudaMemcpyAsync(sv, jsig.get() + (kk > 0 ? kk - 1 : 0), 16, cudaMemcpyDeviceToHost, st));
-      double s1 = 0;
-      CK(cudaMemcpyAsync(&s1, jsig.get(), 8, cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      if (kk > 0 && s1 > 0) min_gap = std::min(min_gap, (sv[0] - sv[1]) / s1);
+    int64_t kk = std::min<int64_t>(target, k + rank);
+    std::vector<double> hs(n);
+    d2h_sync(hs.data(), jsig.get(), size_t(n) * 8, st);
+    if constexpr (sizeof(T) == 4) {
+      // The FP32 Jacobi leaves columns below (n eps) |K|_F unrotated as noise;
+      // their singular vectors are not orthogonal to the rest, so such
+      // directions are never kept.
+      double f2 = 0;
+      for (double v : hs) f2 += v * v;
+      const double floor_ = 2.0 * double(n) * 1.1920928955078125e-07 * std::sqrt(f2);
+      int64_t live = 0;
+      while (live < n && hs[live] > floor_) ++live;
+      kk = std::min(kk, live);
     }
+    if (kk > kmax) fail(FASTPI_ERR_ARG, "internal: basis exceeds its capacity");
+    if (kk < n && kk > 0 && hs[0] > 0) min_gap = std::min(min_gap, (hs[kk - 1] - hs[kk]) / hs[0]);
     // rotations
     DArr<T> Ut(n * std::max<int64_t>(kk, 1), st), Vt(n * std::max<int64_t>(kk, 1), st);
     if (kk > 0) {

@@ -162,9 +162,8 @@ __global__ void __launch_bounds__(256) k_jacobi(const DevProb<T>* __restrict__ p
       const int64_t sweep = t / pr.R;
       const int rr = int(t % pr.R);
       if (rr == 0 && sweep > 0) {
-        double prev = __longlong_as_double(
-            (long long)(*(volatile unsigned long long*)&state[b].offmax[(sweep - 1) % 3]));
-        bool conv = prev <= tol_rel;
+        // converged when the previous sweep made no rotation
+        const bool conv = *(volatile unsigned long long*)&state[b].offmax[(sweep - 1) % 3] == 0ull;
         if (conv || sweep >= max_sweeps) {
           if (slot == 0 && lane == 0) {
             state[b].done = 1;
@@ -220,9 +219,8 @@ __global__ void __launch_bounds__(256) k_jacobi(const DevProb<T>* __restrict__ p
         ga = warp_sum(ga);
         if (double(al) <= pr.tol_abs2 || double(be) <= pr.tol_abs2) continue;
         const double off = fabs(double(ga)) / (sqrt(double(al)) * sqrt(double(be)));
-        if (lane == 0 && off > 0)
-          atomicMax(&state[b].offmax[sweep % 3], (unsigned long long)__double_as_longlong(off));
         if (!(off > tol_rel)) continue;
+        if (lane == 0) *(volatile unsigned long long*)&state[b].offmax[sweep % 3] = 1ull;   // rotated
         const T zeta = (be - al) / (T(2) * ga);
         const T tt = copysign(T(1), zeta) / (fabs(zeta) + hypot(T(1), zeta));
         const T c = T(1) / sqrt(T(1) + tt * tt);
@@ -255,9 +253,8 @@ __global__ void __launch_bounds__(256) k_jacobi(const DevProb<T>* __restrict__ p
       ga = warp_sum(ga);
       if (double(al) <= pr.tol_abs2 || double(be) <= pr.tol_abs2) continue;
       double off = fabs(double(ga)) / (sqrt(double(al)) * sqrt(double(be)));
-      if (lane == 0 && off > 0)
-        atomicMax(&state[b].offmax[sweep % 3], (unsigned long long)__double_as_longlong(off));
       if (!(off > tol_rel)) continue;
+      if (lane == 0) *(volatile unsigned long long*)&state[b].offmax[sweep % 3] = 1ull;   // rotated
       T zeta = (be - al) / (T(2) * ga);
       T tt = copysign(T(1), zeta) / (fabs(zeta) + hypot(T(1), zeta));
       T c = T(1) / sqrt(T(1) + tt * tt);
@@ -408,11 +405,16 @@ JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>
   if (need > 8 && need <= 16) kern = (void*)k_jacobi<T, 16>;
   if constexpr (sizeof(T) == 4) {
     if (need > 16 && need <= 32) kern = (void*)k_jacobi<T, 32>;
+    if (need > 32 && need <= 44) kern = (void*)k_jacobi<T, 44>;
   }
+  // FP64 throughput per SM is low, so FP64 pairs are spread over as many SMs
+  // as possible (two warps per CTA); FP32 packs eight warps per CTA.
+  const int bs = sizeof(T) == 8 ? 64 : 256;
+  const int wpb = bs / 32;
   int occ = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, bs, 0));
   if (occ < 1) occ = 1;
-  int64_t want = (pairs + 7) / 8;
+  int64_t want = (pairs + wpb - 1) / wpb;
   int64_t cap = int64_t(h->num_sms) * occ;
   int grid = int(std::max<int64_t>(1, std::min(want, cap)));
   int64_t max_steps = int64_t(max_sweeps + 2) * maxR + 2;
@@ -431,7 +433,7 @@ JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>
   CK(cudaEventCreate(&ev0));
   CK(cudaEventCreate(&ev1));
   CK(cudaEventRecord(ev0, st));
-  CK(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(256), args, 0, st));
+  CK(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(bs), args, 0, st));
   CK_LAUNCH();
   CK(cudaEventRecord(ev1, st));
 
@@ -463,6 +465,37 @@ JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>
   stats.hit_cap = (stat & ST_JACOBI_SWEEPS) != 0;
   return stats;
 }
+
+template <typename T>
+void jacobi_sort_columns(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& probs, double* sig, int32_t* perm) {
+  const int nprob = int(probs.size());
+  if (nprob == 0) return;
+  cudaStream_t st = h->stream;
+  std::vector<DevProb<T>> dp(nprob);
+  std::vector<int64_t> sig_off(nprob);
+  int64_t soff = 0;
+  int maxq = 1;
+  for (int b = 0; b < nprob; ++b) {
+    dp[b] = DevProb<T>{probs[b].A, probs[b].V, probs[b].lda, probs[b].ldv, probs[b].p, probs[b].q, 0, 0, 0, 0.0};
+    sig_off[b] = soff;
+    soff += probs[b].q;
+    maxq = std::max(maxq, probs[b].q);
+  }
+  if (maxq > 8192) fail(FASTPI_ERR_ARG, "Jacobi SVD: more than 8192 columns in one problem");
+  DArr<DevProb<T>> d_probs(nprob, st);
+  DArr<int64_t> d_sig_off(nprob, st);
+  CK(cudaMemcpyAsync(d_probs.get(), dp.data(), sizeof(DevProb<T>) * nprob, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_sig_off.get(), sig_off.data(), 8 * nprob, cudaMemcpyHostToDevice, st));
+  int nq_max = 1;
+  while (nq_max < maxq) nq_max <<= 1;
+  size_t smem = size_t(nq_max) * (sizeof(double) + sizeof(int));
+  if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_finish<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  k_finish<T><<<nprob, 512, smem, st>>>(d_probs, d_sig_off, sig, perm, nq_max);
+  CK_LAUNCH();
+}
+
+template void jacobi_sort_columns<double>(fastpi_ctx*, const std::vector<JacobiProblem<double>>&, double*, int32_t*);
+template void jacobi_sort_columns<float>(fastpi_ctx*, const std::vector<JacobiProblem<float>>&, double*, int32_t*);
 
 template JacobiStats jacobi_svd_batched<double>(fastpi_ctx*, const std::vector<JacobiProblem<double>>&, double*,
                                                 int32_t*);

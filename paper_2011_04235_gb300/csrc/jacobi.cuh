@@ -29,4 +29,17 @@ template <typename T>
 JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& probs, double* sig,
                                int32_t* perm);
 
+// Only the last step of jacobi_svd_batched: column norms of each (already
+// orthogonalised) A and the descending sort, into sig / perm.
+template <typename T>
+void jacobi_sort_columns(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& probs, double* sig, int32_t* perm);
+
+// FP32 core SVD of one square n x n column-major K (ld n) inside one
+// thread-block cluster (K resident in distributed shared memory).  Same
+// outputs as jacobi_svd_batched for a single problem (V = J, n x n col-major,
+// ld n).  Returns false, having done nothing, when n is too large for the
+// cluster's shared memory or the device cannot host the cluster; the caller
+// then uses jacobi_svd_batched.
+bool jacobi_svd_cluster(fastpi_ctx* h, float* K, float* V, int n, double* sig, int32_t* perm, JacobiStats* stats);
+
 }  // namespace fastpi
