@@ -335,6 +335,122 @@ __global__ void k_pchol(const double* G, int c, const double* dn, double tol, do
 
 // Linv_orig[a, piv[b]] = X[a, b] for a, b < rank (zero elsewhere): the map
 // that turns R (p x c) into Q1 = R Linv_orig^T.
+// Blocked form of k_pchol.  G (c x c, FP64, full symmetric) holds the Schur
+// complement of the columns factored so far (earlier panels are removed from
+// it by a GEMM after each panel); d / used / Lo / piv / kept / rank persist in
+// global memory across the panels.  One CTA factors the panel columns
+// [t0, t0 + nb) with the same pivot rule and drop test as k_pchol: the pivot
+// is the unused column with the largest remaining diagonal (ties to the lower
+// index); when it is <= thr the factorization stops (state[0] = 1).  The
+// panel's columns of Lo are staged in shared memory.
+constexpr int PCHOL_NB = 32;
+__global__ void k_pchol_panel(const double* __restrict__ G, int c, int t0, const double* dn, double tol,
+                              double* d, int32_t* used, double* Lo, int32_t* piv, int32_t* kept, int32_t* state) {
+  extern __shared__ double pan[];   // c x PCHOL_NB: Lo[:, t0 + k]
+  __shared__ double s_best, s_thr;
+  __shared__ int s_arg;
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  if (state[0]) return;   // an earlier panel stopped the factorization
+  const int nb = min(PCHOL_NB, c - t0);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (t0 == 0) {
+    for (int i = threadIdx.x; i < c; i += blockDim.x) {
+      d[i] = G[int64_t(i) * c + i];
+      used[i] = 0;
+      kept[i] = 0;
+      piv[i] = -1;
+    }
+    for (int64_t e = threadIdx.x; e < int64_t(c) * c; e += blockDim.x) Lo[e] = 0.0;
+  }
+  for (int e = threadIdx.x; e < c * PCHOL_NB; e += blockDim.x) pan[e] = 0.0;
+  if (threadIdx.x == 0) {
+    double mx = 0;
+    for (int t = 0; t < c; ++t) mx = fmax(mx, dn[t]);
+    s_thr = tol * tol * mx;
+  }
+  __syncthreads();
+  int stop = 0;
+  for (int k = 0; k < nb; ++k) {
+    const int t = t0 + k;
+    double bv = -1.0;
+    int bi = c;
+    for (int i = threadIdx.x; i < c; i += blockDim.x)
+      if (!used[i] && (d[i] > bv || (d[i] == bv && i < bi))) {
+        bv = d[i];
+        bi = i;
+      }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      red_v[w] = bv;
+      red_i[w] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double v = red_v[0];
+      int ii = red_i[0];
+      for (int q = 1; q < nw; ++q)
+        if (red_v[q] > v || (red_v[q] == v && red_i[q] < ii)) {
+          v = red_v[q];
+          ii = red_i[q];
+        }
+      s_best = v;
+      s_arg = ii;
+    }
+    __syncthreads();
+    if (!(s_best > s_thr) || s_arg >= c) {
+      stop = 1;
+      break;
+    }
+    const int j = s_arg;
+    const double ljj = sqrt(s_best);
+    if (threadIdx.x == 0) {
+      used[j] = 1;
+      piv[t] = j;
+      kept[t] = 1;
+      pan[j * PCHOL_NB + k] = ljj;
+      state[1] = t + 1;   // rank so far
+    }
+    __syncthreads();
+    // column t for every unused row: the Schur complement column of pivot j
+    // (row j of G, by symmetry) minus this panel's earlier columns
+    for (int i = threadIdx.x; i < c; i += blockDim.x) {
+      if (used[i]) continue;
+      double s = G[int64_t(j) * c + i];
+      for (int q = 0; q < k; ++q) s -= pan[i * PCHOL_NB + q] * pan[j * PCHOL_NB + q];
+      const double lit = s / ljj;
+      pan[i * PCHOL_NB + k] = lit;
+      d[i] -= lit * lit;
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < c * nb; e += blockDim.x) {
+    const int i = e / nb, k = e % nb;
+    Lo[int64_t(i) * c + t0 + k] = pan[i * PCHOL_NB + k];
+  }
+  if (threadIdx.x == 0 && stop) state[0] = 1;
+}
+
+// Lp[a, b] = Lo[piv[a], b] for b <= a < rank (zero elsewhere); rank = state[1].
+__global__ void k_gather_lp(const double* Lo, const int32_t* piv, const int32_t* state, int c, double* Lp,
+                            int32_t* rank_out) {
+  const int rank = state[1];
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < int64_t(c) * c;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int a = int(e / c), b = int(e % c);
+    Lp[e] = (a < rank && b <= a) ? Lo[int64_t(piv[a]) * c + b] : 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *rank_out = rank;
+}
+
 // One CTA.
 __global__ void k_scatter_inv(const double* X, const int32_t* piv, const int32_t* rank_p, int c, double* Lio) {
   const int rank = *rank_p;
@@ -528,9 +644,29 @@ struct Phase {
       }
     };
     gram(D.get(), G.get());
-    k_pchol<<<1, 1024, size_t(c) * 12, st>>>(G.get(), int(c), dn.get(), drop_tol, Lo.get(), Lp.get(), kept.get(),
-                                             piv.get(), rk.get());
-    CK_LAUNCH();
+    const size_t pan_bytes = size_t(c) * PCHOL_NB * sizeof(double);
+    if (pan_bytes <= 200 * 1024) {
+      // blocked: panels of PCHOL_NB columns in one CTA, trailing updates as FP64 GEMMs
+      DArr<double> dd(c, st);
+      DArr<int32_t> used(c, st), pstate(2, st);
+      CK(cudaMemsetAsync(pstate.get(), 0, 8, st));
+      if (pan_bytes > 48 * 1024)
+        CK(cudaFuncSetAttribute(k_pchol_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pan_bytes)));
+      for (int64_t t0 = 0; t0 < c; t0 += PCHOL_NB) {
+        k_pchol_panel<<<1, 1024, pan_bytes, st>>>(G.get(), int(c), int(t0), dn.get(), drop_tol, dd.get(),
+                                                  used.get(), Lo.get(), piv.get(), kept.get(), pstate.get());
+        CK_LAUNCH();
+        const int64_t nbp = std::min<int64_t>(PCHOL_NB, c - t0);
+        if (t0 + nbp < c)
+          gemm<double>(st, false, true, c, c, nbp, -1.0, Lo.get() + t0, c, Lo.get() + t0, c, 1.0, G.get(), c);
+      }
+      k_gather_lp<<<g1(c * c), 256, 0, st>>>(Lo.get(), piv.get(), pstate.get(), int(c), Lp.get(), rk.get());
+      CK_LAUNCH();
+    } else {
+      k_pchol<<<1, 1024, size_t(c) * 12, st>>>(G.get(), int(c), dn.get(), drop_tol, Lo.get(), Lp.get(), kept.get(),
+                                               piv.get(), rk.get());
+      CK_LAUNCH();
+    }
     trinv(Lp.get(), kept.get(), X.get());
     k_scatter_inv<<<1, 1024, 0, st>>>(X.get(), piv.get(), rk.get(), int(c), Linv.get());
     CK_LAUNCH();

@@ -145,16 +145,53 @@ __global__ void k_init_v(const DevProb<T>* probs) {
   }
 }
 
-template <typename T, int MAXV>
+__device__ __forceinline__ void team_bar(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Sum of three values over a team of NW warps (warp shuffles, then shared
+// memory across the team's warps, synchronised by the team's named barrier).
+template <typename T, int NW>
+__device__ __forceinline__ void team_sum3(T& a, T& b, T& c, int tm, T* red) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  if constexpr (NW > 1) {
+    const int lane = threadIdx.x & 31, wi = (threadIdx.x >> 5) % NW;
+    T* r = red + tm * NW * 3;
+    if (lane == 0) {
+      r[wi * 3] = a;
+      r[wi * 3 + 1] = b;
+      r[wi * 3 + 2] = c;
+    }
+    team_bar(1 + tm, 32 * NW);
+    a = b = c = T(0);
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+      a += r[q * 3];
+      b += r[q * 3 + 1];
+      c += r[q * 3 + 2];
+    }
+    team_bar(1 + tm, 32 * NW);
+  }
+}
+
+// One pair of columns per team of NW warps; team-lane tl owns rows
+// tl, tl + 32 NW, ...  Every decision below depends only on values that are
+// identical across the team, so the team's threads always take the same path.
+template <typename T, int MAXV, int NW>
 __global__ void __launch_bounds__(256) k_jacobi(const DevProb<T>* __restrict__ probs, const int64_t* __restrict__ pair_off,
                                                 int nprob, int64_t total_pairs, ProbState* state, GridBar* gb,
                                                 int max_sweeps, int64_t max_steps, double tol_rel,
                                                 unsigned* status) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  constexpr int TS = 32 * NW;
+  __shared__ T red[(256 / TS) * NW * 3];
+  const int tl = threadIdx.x % TS, tm = threadIdx.x / TS;
+  const int64_t teams_per_cta = blockDim.x / TS;
+  const int64_t gt = int64_t(blockIdx.x) * teams_per_cta + tm;
+  const int64_t nteams = int64_t(gridDim.x) * teams_per_cta;
   for (int64_t t = 0; t < max_steps; ++t) {
-    for (int64_t w = gw; w < total_pairs; w += nw) {
+    for (int64_t w = gt; w < total_pairs; w += nteams) {
       const int b = find_prob(pair_off, nprob, w);
       const DevProb<T> pr = probs[b];
       if (*(volatile int*)&state[b].done) continue;
@@ -165,7 +202,7 @@ __global__ void __launch_bounds__(256) k_jacobi(const DevProb<T>* __restrict__ p
         // converged when the previous sweep made no rotation
         const bool conv = *(volatile unsigned long long*)&state[b].offmax[(sweep - 1) % 3] == 0ull;
         if (conv || sweep >= max_sweeps) {
-          if (slot == 0 && lane == 0) {
+          if (slot == 0 && tl == 0) {
             state[b].done = 1;
             state[b].sweeps = int(sweep);
             atomicAdd(&gb->done_count, 1);
@@ -173,7 +210,7 @@ __global__ void __launch_bounds__(256) k_jacobi(const DevProb<T>* __restrict__ p
           }
           continue;
         }
-        if (slot == 0 && lane == 0) state[b].offmax[(sweep + 1) % 3] = 0ull;
+        if (slot == 0 && tl == 0) state[b].offmax[(sweep + 1) % 3] = 0ull;
       }
       const int qe = pr.qe;
       int i, j;
@@ -194,13 +231,13 @@ __global__ void __launch_bounds__(256) k_jacobi(const DevProb<T>* __restrict__ p
       T* aj = pr.A + int64_t(j) * pr.lda;
       T* vi = pr.V + int64_t(i) * pr.ldv;
       T* vj = pr.V + int64_t(j) * pr.ldv;
-      if (pr.p <= 32 * MAXV && pr.q <= 32 * MAXV) {
+      if (pr.p <= TS * MAXV && pr.q <= TS * MAXV) {
         // register-resident pair: every load of the two columns of A and of V
         // is issued before the first use, so a round costs one L2 round trip
         T xa[MAXV], ya[MAXV], xv[MAXV], yv[MAXV];
 #pragma unroll
         for (int u = 0; u < MAXV; ++u) {
-          const int r = lane + 32 * u;
+          const int r = tl + TS * u;
           const bool ok = r < pr.p, okv = r < pr.q;
           xa[u] = ok ? __ldcg(ai + r) : T(0);
           ya[u] = ok ? __ldcg(aj + r) : T(0);
@@ -214,20 +251,18 @@ __global__ void __launch_bounds__(256) k_jacobi(const DevProb<T>* __restrict__ p
           be = fma(ya[u], ya[u], be);
           ga = fma(xa[u], ya[u], ga);
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
+        team_sum3<T, NW>(al, be, ga, tm, red);
         if (double(al) <= pr.tol_abs2 || double(be) <= pr.tol_abs2) continue;
         const double off = fabs(double(ga)) / (sqrt(double(al)) * sqrt(double(be)));
         if (!(off > tol_rel)) continue;
-        if (lane == 0) *(volatile unsigned long long*)&state[b].offmax[sweep % 3] = 1ull;   // rotated
+        if (tl == 0) *(volatile unsigned long long*)&state[b].offmax[sweep % 3] = 1ull;   // rotated
         const T zeta = (be - al) / (T(2) * ga);
         const T tt = copysign(T(1), zeta) / (fabs(zeta) + hypot(T(1), zeta));
         const T c = T(1) / sqrt(T(1) + tt * tt);
         const T s = c * tt;
 #pragma unroll
         for (int u = 0; u < MAXV; ++u) {
-          const int r = lane + 32 * u;
+          const int r = tl + TS * u;
           if (r < pr.p) {
             __stcg(ai + r, c * xa[u] - s * ya[u]);
             __stcg(aj + r, s * xa[u] + c * ya[u]);
@@ -242,31 +277,29 @@ __global__ void __launch_bounds__(256) k_jacobi(const DevProb<T>* __restrict__ p
       // long columns: two passes over L2, loads unrolled four deep
       T al = 0, be = 0, ga = 0;
 #pragma unroll 4
-      for (int r = lane; r < pr.p; r += 32) {
+      for (int r = tl; r < pr.p; r += TS) {
         T x = __ldcg(ai + r), y = __ldcg(aj + r);
         al = fma(x, x, al);
         be = fma(y, y, be);
         ga = fma(x, y, ga);
       }
-      al = warp_sum(al);
-      be = warp_sum(be);
-      ga = warp_sum(ga);
+      team_sum3<T, NW>(al, be, ga, tm, red);
       if (double(al) <= pr.tol_abs2 || double(be) <= pr.tol_abs2) continue;
       double off = fabs(double(ga)) / (sqrt(double(al)) * sqrt(double(be)));
       if (!(off > tol_rel)) continue;
-      if (lane == 0) *(volatile unsigned long long*)&state[b].offmax[sweep % 3] = 1ull;   // rotated
+      if (tl == 0) *(volatile unsigned long long*)&state[b].offmax[sweep % 3] = 1ull;   // rotated
       T zeta = (be - al) / (T(2) * ga);
       T tt = copysign(T(1), zeta) / (fabs(zeta) + hypot(T(1), zeta));
       T c = T(1) / sqrt(T(1) + tt * tt);
       T s = c * tt;
 #pragma unroll 4
-      for (int r = lane; r < pr.p; r += 32) {
+      for (int r = tl; r < pr.p; r += TS) {
         T x = __ldcg(ai + r), y = __ldcg(aj + r);
         __stcg(ai + r, c * x - s * y);
         __stcg(aj + r, s * x + c * y);
       }
 #pragma unroll 4
-      for (int r = lane; r < pr.q; r += 32) {
+      for (int r = tl; r < pr.q; r += TS) {
         T x = __ldcg(vi + r), y = __ldcg(vj + r);
         __stcg(vi + r, c * x - s * y);
         __stcg(vj + r, s * x + c * y);
@@ -399,22 +432,36 @@ JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>
 
   const int max_sweeps = sizeof(T) == 8 ? 40 : 30;
   const double tol_rel = std::sqrt(double(maxp)) * Eps<T>::v;
-  // registers per lane per column: the smallest that holds the longest column
-  const int need = (std::max(maxp, maxq) + 31) / 32;
-  void* kern = (void*)k_jacobi<T, 8>;   // also the kernel for long columns (two-pass path)
-  if (need > 8 && need <= 16) kern = (void*)k_jacobi<T, 16>;
+  // FP32: one warp per pair, eight pairs per CTA, registers per lane = the
+  // smallest of {8, 16, 32, 44} that holds the longest column.  FP64: the
+  // FP64 rate per SM is low, so a pair is shared by a team of 2 or 4 warps
+  // (one team per CTA, spreading pairs over the SMs) holding 16 values per lane.
+  const int maxdim = std::max(maxp, maxq);
+  void* kern = nullptr;
+  int bs = 256, pairs_per_cta = 8;
   if constexpr (sizeof(T) == 4) {
-    if (need > 16 && need <= 32) kern = (void*)k_jacobi<T, 32>;
-    if (need > 32 && need <= 44) kern = (void*)k_jacobi<T, 44>;
+    const int need = (maxdim + 31) / 32;
+    kern = (void*)k_jacobi<T, 8, 1>;   // also the kernel for long columns (two-pass path)
+    if (need > 8 && need <= 16) kern = (void*)k_jacobi<T, 16, 1>;
+    if (need > 16 && need <= 32) kern = (void*)k_jacobi<T, 32, 1>;
+    if (need > 32 && need <= 44) kern = (void*)k_jacobi<T, 44, 1>;
+  } else {
+    pairs_per_cta = 1;
+    if (maxdim <= 64 * 8) {
+      kern = (void*)k_jacobi<T, 8, 2>;
+      bs = 64;
+    } else if (maxdim <= 64 * 16) {
+      kern = (void*)k_jacobi<T, 16, 2>;
+      bs = 64;
+    } else {
+      kern = (void*)k_jacobi<T, 16, 4>;   // register path up to 2048 rows, two-pass beyond
+      bs = 128;
+    }
   }
-  // FP64 throughput per SM is low, so FP64 pairs are spread over as many SMs
-  // as possible (two warps per CTA); FP32 packs eight warps per CTA.
-  const int bs = sizeof(T) == 8 ? 64 : 256;
-  const int wpb = bs / 32;
   int occ = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, bs, 0));
   if (occ < 1) occ = 1;
-  int64_t want = (pairs + wpb - 1) / wpb;
+  int64_t want = (pairs + pairs_per_cta - 1) / pairs_per_cta;
   int64_t cap = int64_t(h->num_sms) * occ;
   int grid = int(std::max<int64_t>(1, std::min(want, cap)));
   int64_t max_steps = int64_t(max_sweeps + 2) * maxR + 2;
