@@ -32,6 +32,7 @@ namespace {
 constexpr int CT = 512;      // threads per CTA
 constexpr int MAXCL = 16;    // CTAs per cluster
 constexpr int MAX_SWEEPS = 30;
+constexpr float EARLY_OFF = 1e-4f;   // see the end-of-sweep test
 constexpr int REPLAY_ROWS = 8;
 constexpr int REPLAY_BATCH = 16;   // rounds of rotations staged in shared memory at once
 
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(CT, 1) k_jacobi_cluster(CArgs a) {
             const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + hypotf(1.f, zeta));
             c = 1.f / sqrtf(1.f + tt * tt);
             s = c * tt;
-            if (src == 0) s_rot = 1;
+            if (src == 0) s_rot = off > EARLY_OFF ? 2 : max(s_rot, 1);
           }
         }
         if (src < CL) cl.map_shared_rank(rot, src)[slot] = make_float2(c, s);   // one 64-bit DSMEM store
@@ -202,11 +203,14 @@ __global__ void __launch_bounds__(CT, 1) k_jacobi_cluster(CArgs a) {
       if (tid < CL) cl.map_shared_rank(flg, tid)[par * MAXCL + rank] = s_rot;
       cl.sync();
       int any = 0;
-      for (int q = 0; q < CL; ++q) any |= flg[par * MAXCL + q];
+      for (int q = 0; q < CL; ++q) any = max(any, flg[par * MAXCL + q]);
       __syncthreads();
       if (tid == 0) s_rot = 0;
       ++sweep;
-      if (!any) break;
+      // converged: no rotation at all in this sweep, or only rotations with
+      // off <= EARLY_OFF -- in the quadratic phase of convergence the next
+      // sweep would then meet off ~ EARLY_OFF^2 < tol and rotate nothing
+      if (any < 2) break;
       if (sweep >= MAX_SWEEPS) {
         if (rank == 0 && tid == 0) atomicOr(a.status, ST_JACOBI_SWEEPS);
         break;
