@@ -190,6 +190,21 @@ typedef struct {
 fastpi_status fastpi_get_counters(fastpi_counters* out);   /* host struct */
 void fastpi_reset_counters(void);
 
+/* Diagnostic entry point (no citation: it exposes the library's internal
+ * FP32 dense kernel so that it can be checked on its own).
+ * C (M x N) = alpha * op(A) op(B) + beta * C on device float32 row-major
+ * arrays: op(A) = A (M x K, lda) or, with ta != 0, A^T of a K x M array;
+ * op(B) = B (K x N, ldb) or, with tb != 0, B^T of an N x K array.
+ * engine 0: SIMT FP32 kernel; 1: tcgen05 TF32 kernel with operands rounded
+ * to TF32 (one tensor pass); 3: tcgen05 TF32 kernel with split hi + lo
+ * operands (three tensor passes, FP32-level accuracy).  The tensor engines
+ * return FASTPI_ERR_ARG on devices other than sm_103 (and for M, N or K of
+ * 2^31 or more).  Scratch is allocated on the stream; the call returns
+ * after the stream has finished (it checks the kernels' status word). */
+fastpi_status fastpi_gemm_f32(int ta, int tb, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+                              int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                              int engine, void* cuda_stream);
+
 /* Message of the last failed call on h (or of the last failed fastpi_create
  * when h is NULL).  Never NULL; valid until the next call on h. */
 const char* fastpi_last_error(fastpi_t h);

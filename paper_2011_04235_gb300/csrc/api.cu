@@ -259,6 +259,36 @@ fastpi_status fastpi_get_counters(fastpi_counters* out) {
 
 void fastpi_reset_counters(void) { reset_counters(); }
 
+fastpi_status fastpi_gemm_f32(int ta, int tb, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+                              int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                              int engine, void* cuda_stream) {
+  try {
+    require(M >= 0 && N >= 0 && K >= 0, FASTPI_ERR_ARG, "negative size");
+    require(engine == 0 || engine == 1 || engine == 3, FASTPI_ERR_ARG, "engine must be 0, 1 or 3");
+    require(ldc >= N && lda >= (ta ? M : K) && ldb >= (tb ? K : N), FASTPI_ERR_ARG, "leading dimension too small");
+    require(M * N == 0 || C != nullptr, FASTPI_ERR_ARG, "C is NULL");
+    require(M * N * K == 0 || (A != nullptr && B != nullptr), FASTPI_ERR_ARG, "A or B is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (engine == 0) {
+      gemm<float>(st, ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    } else {
+      require(M * N == 0 || K == 0 || gemm_tf32_supported(ta != 0, tb != 0, M, N, K, lda, ldb, ldc, A, B, C),
+              FASTPI_ERR_ARG, "the tensor-core GEMM needs an sm_103 device and sizes below 2^31");
+      gemm_tf32(st, ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, engine);
+    }
+    CK(cudaStreamSynchronize(st));
+    const unsigned stat = gemm_tc_status(st, true);
+    require(stat == 0, FASTPI_ERR_CUDA, "tensor-core GEMM: a bounded wait ran out");
+  } catch (const Error& e) {
+    g_create_error = e.msg;
+    return e.status;
+  } catch (const std::exception& e) {
+    g_create_error = e.what();
+    return FASTPI_ERR_CUDA;
+  }
+  return FASTPI_OK;
+}
+
 const char* fastpi_last_error(fastpi_t h) {
   if (!h) return g_create_error.c_str();
   return h->last_error.c_str();

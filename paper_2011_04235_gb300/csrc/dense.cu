@@ -204,6 +204,15 @@ void gemm(cudaStream_t st, bool ta, bool tb, int64_t M, int64_t N, int64_t K, T 
   gemm_mixed<T, T>(st, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
+void gemm_f32(cudaStream_t st, bool ta, bool tb, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+              int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc) {
+  const double work = 2.0 * double(M) * double(N) * double(K);
+  if (M >= 64 && work >= double(1 << 24) && gemm_tf32_supported(ta, tb, M, N, K, lda, ldb, ldc, A, B, C))
+    gemm_tf32(st, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 3);
+  else
+    gemm<float>(st, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
 template void gemm_mixed<float, double>(cudaStream_t, bool, bool, int64_t, int64_t, int64_t, double, const float*,
                                         int64_t, const float*, int64_t, double, double*, int64_t);
 

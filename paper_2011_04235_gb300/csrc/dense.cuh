@@ -21,12 +21,22 @@ void gemm_mixed(cudaStream_t st, bool ta, bool tb, int64_t M, int64_t N, int64_t
                 int64_t lda, const TI* B, int64_t ldb, T beta, T* C, int64_t ldc);
 
 // Same contract with FP32 storage on the TF32 tensor cores (tcgen05.mma,
-// kind::tf32, FP32 accumulation in tensor memory).  Falls back to nothing:
-// callers use it only when the shape is supported (see gemm_tf32_supported).
+// kind::tf32, FP32 accumulation in tensor memory, TMA-staged operands).
+// passes = 1: operands rounded to TF32; passes = 3: split hi + lo TF32
+// products (FP32-level accuracy).  gemm_tf32_supported says whether the
+// device and the sizes allow the tensor path.
 bool gemm_tf32_supported(bool ta, bool tb, int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb,
                          int64_t ldc, const void* A, const void* B, const void* C);
 void gemm_tf32(cudaStream_t st, bool ta, bool tb, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
-               int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc);
+               int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc, int passes);
+// Status bits raised by the tensor-core GEMM kernels since the last clear
+// (synchronizes the stream).
+unsigned gemm_tc_status(cudaStream_t st, bool clear);
+
+// FP32 GEMM of the mixed-precision form: the tensor-core path for shapes with
+// enough work to fill it (2 M N K >= 2^24 and M >= 64), SIMT FP32 otherwise.
+void gemm_f32(cudaStream_t st, bool ta, bool tb, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+              int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc);
 
 // dst[i*ldd + j] = (T)src[i*lds + j] for a rows x cols block.
 template <typename Td, typename Ts>

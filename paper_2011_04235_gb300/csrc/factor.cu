@@ -35,6 +35,18 @@ constexpr int64_t DEFAULT_CHUNK = 256;    // border rows / columns per append st
 
 inline unsigned g1(int64_t n, int bs = 256) { return n > 0 ? unsigned((n + bs - 1) / bs) : 1u; }
 
+// Dense products of the updates: FP64 SIMT in the FP64 form; in the mixed
+// form the FP32 products go to the TF32 tensor cores (split hi + lo passes)
+// when the shape has enough work.
+template <typename T>
+inline void gemm_t(cudaStream_t st, bool ta, bool tb, int64_t M, int64_t N, int64_t K, T alpha, const T* A,
+                   int64_t lda, const T* B, int64_t ldb, T beta, T* C, int64_t ldc) {
+  if constexpr (std::is_same<T, float>::value)
+    gemm_f32(st, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else
+    gemm<T>(st, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
 struct BlkDesc {
   int64_t m_b, n_b, s_b, ro, co, soff, data_off, v_off, u_off, sig_off;
 };
@@ -607,9 +619,9 @@ struct Phase {
       k_spmm_t<T><<<unsigned(c), 256, 0, st>>>(sc.ptr, sc.idx, sc.val, a, k, Ucur, kmax, Pt.get(), ldp);
       CK_LAUNCH();
       // R = D - Uc P ; second projection pass
-      gemm<T>(st, false, true, p, c, k, T(-1), Ucur, kmax, Pt.get(), ldp, T(1), D.get(), c);
-      gemm<T>(st, true, false, c, k, p, T(1), D.get(), c, Ucur, kmax, T(0), P2t.get(), ldp);
-      gemm<T>(st, false, true, p, c, k, T(-1), Ucur, kmax, P2t.get(), ldp, T(1), D.get(), c);
+      gemm_t<T>(st, false, true, p, c, k, T(-1), Ucur, kmax, Pt.get(), ldp, T(1), D.get(), c);
+      gemm_t<T>(st, true, false, c, k, p, T(1), D.get(), c, Ucur, kmax, T(0), P2t.get(), ldp);
+      gemm_t<T>(st, false, true, p, c, k, T(-1), Ucur, kmax, P2t.get(), ldp, T(1), D.get(), c);
       k_axpy2d<T><<<g1(c * k), 256, 0, st>>>(c, k, P2t.get(), ldp, Pt.get(), ldp);
       CK_LAUNCH();
     }
@@ -671,10 +683,10 @@ struct Phase {
     k_scatter_inv<<<1, 1024, 0, st>>>(X.get(), piv.get(), rk.get(), int(c), Linv.get());
     CK_LAUNCH();
     to_T(Linv.get(), LinvT.get());
-    gemm<T>(st, false, true, p, c, c, T(1), D.get(), c, LinvT.get(), c, T(0), Q1.get(), c);
+    gemm_t<T>(st, false, true, p, c, c, T(1), D.get(), c, LinvT.get(), c, T(0), Q1.get(), c);
     // second pass: Q1 is orthonormal up to rounding, its Gram ~ I is well
     // conditioned, so this Cholesky runs in the storage precision
-    gemm<T>(st, true, false, c, c, p, T(1), Q1.get(), c, Q1.get(), c, T(0), GT.get(), c);
+    gemm_t<T>(st, true, false, c, c, p, T(1), Q1.get(), c, Q1.get(), c, T(0), GT.get(), c);
     const size_t packed = size_t(c) * (c + 1) / 2 * sizeof(T);
     if (packed <= 200 * 1024) {
       if (packed > 48 * 1024)
@@ -686,7 +698,7 @@ struct Phase {
       CK_LAUNCH();
     }
     trinv(GT.get(), kept2.get(), LinvT.get());
-    gemm<T>(st, false, true, p, c, c, T(1), Q1.get(), c, LinvT.get(), c, T(0), Q.get(), c);
+    gemm_t<T>(st, false, true, p, c, c, T(1), Q1.get(), c, LinvT.get(), c, T(0), Q.get(), c);
     if (sizeof(T) == 8) {
       CK(cudaMemcpyAsync(G2.get(), GT.get(), size_t(c * c) * 8, cudaMemcpyDeviceToDevice, st));
     } else {
@@ -742,9 +754,9 @@ struct Phase {
     const int nx = cur ^ 1;
     T* Unew = Uc[nx].get();
     T* Wnew = W[nx].get();
-    gemm<T>(st, false, false, p, kk, k, T(1), Ucur, kmax, Ut.get(), kk, T(0), Unew, kmax);
-    gemm<T>(st, false, false, p, kk, c, T(1), Q.get(), c, Ut.get() + k * kk, kk, T(1), Unew, kmax);
-    gemm<T>(st, false, false, q, kk, k, T(1), Wm(), kmax, Vt.get(), kk, T(0), Wnew, kmax);
+    gemm_t<T>(st, false, false, p, kk, k, T(1), Ucur, kmax, Ut.get(), kk, T(0), Unew, kmax);
+    gemm_t<T>(st, false, false, p, kk, c, T(1), Q.get(), c, Ut.get() + k * kk, kk, T(1), Unew, kmax);
+    gemm_t<T>(st, false, false, q, kk, k, T(1), Wm(), kmax, Vt.get(), kk, T(0), Wnew, kmax);
     copy2d<T, T>(st, c, kk, Vt.get() + k * kk, kk, Wnew + q * kmax, kmax);
     CK(cudaMemcpyAsync(sig[nx].get(), jsig.get(), size_t(std::max<int64_t>(kk, 1)) * 8, cudaMemcpyDeviceToDevice,
                        st));
@@ -938,7 +950,7 @@ void factor_impl(fastpi_ctx* h, Factors& F, int64_t r, double kratio, int64_t ch
   tm.start();
   const int64_t rank = colp.k;
   DArr<T> Vnew(n * std::max<int64_t>(rank, 1), st);
-  gemm<T>(st, false, false, n1, rank, s, T(1), rowp.U(), kmax_r, colp.Wm(), kmax_c, T(0), Vnew.get(),
+  gemm_t<T>(st, false, false, n1, rank, s, T(1), rowp.U(), kmax_r, colp.Wm(), kmax_c, T(0), Vnew.get(),
           std::max<int64_t>(rank, 1));
   copy2d<T, T>(st, n2, rank, colp.Wm() + s * kmax_c, kmax_c, Vnew.get() + n1 * std::max<int64_t>(rank, 1),
                std::max<int64_t>(rank, 1));
@@ -962,6 +974,7 @@ void factor_impl(fastpi_ctx* h, Factors& F, int64_t r, double kratio, int64_t ch
   }
   CK(cudaStreamSynchronize(st));
   info.ms_finalize = tm.stop();
+  if (gemm_tc_status(st, true) != 0) fail(FASTPI_ERR_CUDA, "tensor-core GEMM: a bounded wait ran out");
   F.m = m;
   F.n = n;
   F.rank = rank;
@@ -1093,10 +1106,10 @@ void apply_dense(fastpi_ctx* h, const double* Y, int64_t L, int64_t ldy, double*
   } else {
     DArr<float> Yf(m * L, st), Wt(std::max<int64_t>(r, 1) * L, st), Zf(n * L, st);
     copy2d<float, double>(st, m, L, Y, ldy, Yf.get(), L);
-    gemm<float>(st, true, false, r, L, m, 1.f, F.U32.get(), std::max<int64_t>(r, 1), Yf.get(), L, 0.f, Wt.get(), L);
+    gemm_f32(st, true, false, r, L, m, 1.f, F.U32.get(), std::max<int64_t>(r, 1), Yf.get(), L, 0.f, Wt.get(), L);
     k_scale_rows<float><<<g1(r * L), 256, 0, st>>>(r, L, F.S_d.get(), tau, Wt.get(), L);
     CK_LAUNCH();
-    gemm<float>(st, false, false, n, L, r, 1.f, F.V32.get(), std::max<int64_t>(r, 1), Wt.get(), L, 0.f, Zf.get(), L);
+    gemm_f32(st, false, false, n, L, r, 1.f, F.V32.get(), std::max<int64_t>(r, 1), Wt.get(), L, 0.f, Zf.get(), L);
     copy2d<double, float>(st, n, L, Zf.get(), L, Z, ldz);
   }
 }
@@ -1154,7 +1167,7 @@ void apply_csr(fastpi_ctx* h, int64_t L, int64_t nnz_y, const int64_t* yrowptr, 
     CK_LAUNCH();
     k_scale_cols<float><<<g1(L * r), 256, 0, st>>>(L, r, F.S_d.get(), tau, WtT.get());
     CK_LAUNCH();
-    gemm<float>(st, false, true, n, L, r, 1.f, F.V32.get(), ldr, WtT.get(), ldr, 0.f, Zf.get(), L);
+    gemm_f32(st, false, true, n, L, r, 1.f, F.V32.get(), ldr, WtT.get(), ldr, 0.f, Zf.get(), L);
     copy2d<double, float>(st, n, L, Zf.get(), L, Z, ldz);
   }
 }

@@ -29,7 +29,7 @@ SYMBOLS = ["fastpi_create", "fastpi_factor", "fastpi_apply", "fastpi_apply_host"
            "fastpi_residual", "fastpi_residual_noalloc", "fastpi_get_rank", "fastpi_get_S", "fastpi_get_U",
            "fastpi_get_V",
            "fastpi_get_perm", "fastpi_get_blocks", "fastpi_get_info", "fastpi_get_counters",
-           "fastpi_reset_counters", "fastpi_last_error", "fastpi_destroy"]
+           "fastpi_reset_counters", "fastpi_gemm_f32", "fastpi_last_error", "fastpi_destroy"]
 
 
 class FastPIError(RuntimeError):
@@ -78,6 +78,27 @@ def residual_noalloc(m: int, n: int, rowptr: torch.Tensor, col: torch.Tensor, va
     return out.value
 
 
+ENGINES = {"simt": 0, "tf32": 1, "tf32x3": 3}
+
+
+def gemm_f32(A: torch.Tensor, B: torch.Tensor, ta: bool = False, tb: bool = False, engine: str = "tf32x3",
+             alpha: float = 1.0, beta: float = 0.0, Cout: torch.Tensor | None = None) -> torch.Tensor:
+    """C = alpha op(A) op(B) + beta C through fastpi_gemm_f32 (device float32
+    row-major tensors with unit column stride; op = transpose when ta / tb)."""
+    M = A.shape[1] if ta else A.shape[0]
+    K = A.shape[0] if ta else A.shape[1]
+    N = B.shape[0] if tb else B.shape[1]
+    if (B.shape[1] if tb else B.shape[0]) != K:
+        raise ValueError("inner dimensions differ")
+    if Cout is None:
+        Cout = torch.zeros(M, N, dtype=torch.float32, device=A.device)
+    st = torch.cuda.current_stream(A.device).cuda_stream
+    with torch.cuda.device(A.device):
+        _check(lib().fastpi_gemm_f32(int(ta), int(tb), M, N, K, float(alpha), _ptr(A), A.stride(0), _ptr(B),
+                                     B.stride(0), float(beta), _ptr(Cout), Cout.stride(0), ENGINES[engine], st))
+    return Cout
+
+
 def load_library(path: str = LIB_PATH) -> C.CDLL:
     if not os.path.exists(path):
         raise ImportError(f"libfastpi.so not built at {path}; run python -m paper_2011_04235_gb300.build")
@@ -91,6 +112,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fastpi_apply_csr": ([p, i64, i64, vp, vp, vp, vp, i64], i32),
         "fastpi_residual": ([p, vp, i64, i64, vp, i64, C.POINTER(dbl)], i32),
         "fastpi_residual_noalloc": ([i64, i64, vp, vp, vp, vp, i64, i64, vp, i64, C.POINTER(dbl), vp], i32),
+        "fastpi_gemm_f32": ([i32, i32, i64, i64, i64, C.c_float, vp, i64, vp, i64, C.c_float, vp, i64, i32, vp],
+                            i32),
         "fastpi_get_rank": ([p, C.POINTER(i64)], i32),
         "fastpi_get_S": ([p, vp], i32),
         "fastpi_get_U": ([p, vp, i64], i32),
