@@ -239,6 +239,13 @@ def factor(m: int, n: int, rowptr, col, val, r: int, k: float,
     U1, sig1, V1, _ = block_svd(A11, reo, r, n)
     S = sig1.size
     s = int(min(ceil_alpha(n1, r, n), S + m2, n1))
+    sig1_blocks = sig1
+    if not single_shot and chunk_row and 0 < chunk_row < m2 and S > s:
+        # several appends: the running SVD of Eq. 2 holds rank s between
+        # appends, and the block SVD is its initial state, so it starts as the
+        # s largest block triplets (descending; equal values: lower index first)
+        keep = _truncate(sig1, s)
+        U1, sig1, V1 = U1[:, keep], sig1[keep], V1[:, keep]
     gaps: list = []
     if single_shot:
         Urow, sig_row, Vrow = row_update_single(U1, sig1, V1, A21, s)
@@ -252,7 +259,7 @@ def factor(m: int, n: int, rowptr, col, val, r: int, k: float,
     # back to the caller's row / column order
     U_orig = U[reo.row_pos]
     V_orig = V[reo.col_pos]
-    return Factorization(reo, U_orig, sig, V_orig, sig1, s, rr, gaps)
+    return Factorization(reo, U_orig, sig, V_orig, sig1_blocks, s, rr, gaps)
 
 
 def pinv_threshold(S: np.ndarray, m: int, n: int) -> float:

@@ -54,8 +54,8 @@ struct BlkDesc {
 // ----------------------------------------------------------------- blocks (Eq. 1)
 template <typename T>
 __global__ void k_block_out(const BlkDesc* __restrict__ d, const T* __restrict__ data, const T* __restrict__ vbuf,
-                            const double* __restrict__ sig, const int32_t* __restrict__ perm, int64_t S, T* V1,
-                            T* U1, double* Sig1) {
+                            const double* __restrict__ sig, const int32_t* __restrict__ perm,
+                            const int32_t* __restrict__ pos, int64_t ldv, T* V1, T* U1, double* Sig1) {
   const BlkDesc b = d[blockIdx.x];
   const bool tall = b.m_b >= b.n_b;
   const int64_t p = tall ? b.m_b : b.n_b, q = tall ? b.n_b : b.m_b;
@@ -65,12 +65,21 @@ __global__ void k_block_out(const BlkDesc* __restrict__ d, const T* __restrict__
     const int32_t src = perm[b.sig_off + t];
     const double s = sig[b.sig_off + t];
     const T inv = s > 0 ? T(1.0 / s) : T(0);
-    if (threadIdx.x == 0) Sig1[b.soff + t] = s;
+    const int32_t g = pos[b.soff + t];   // column of this triplet in the row-phase state, -1: not kept
     for (int64_t li = threadIdx.x; li < b.m_b; li += blockDim.x)
       U1[b.u_off + li * b.s_b + t] = tall ? B[int64_t(src) * p + li] * inv : J[int64_t(src) * q + li];
+    if (g < 0) continue;
+    if (threadIdx.x == 0) Sig1[g] = s;
     for (int64_t j = threadIdx.x; j < b.n_b; j += blockDim.x)
-      V1[(b.co + j) * S + b.soff + t] = tall ? J[int64_t(src) * q + j] : B[int64_t(src) * p + j] * inv;
+      V1[(b.co + j) * ldv + g] = tall ? J[int64_t(src) * q + j] : B[int64_t(src) * p + j] * inv;
   }
+}
+
+// W[g, pos[g]] = 1 for the kept block triplets (W zeroed before).
+template <typename T>
+__global__ void k_select_w(const int32_t* __restrict__ pos, int64_t S, T* W, int64_t ldw) {
+  const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (g < S && pos[g] >= 0) W[g * ldw + pos[g]] = T(1);
 }
 
 __global__ void k_blk_of_row(const int64_t* off, int64_t B, int32_t* blk_of) {
@@ -882,32 +891,55 @@ void factor_impl(fastpi_ctx* h, Factors& F, int64_t r, double kratio, int64_t ch
   DArr<double> bsig(std::max<int64_t>(sigtot, 1), st);
   DArr<int32_t> bperm(std::max<int64_t>(sigtot, 1), st);
   JacobiStats bjs = jacobi_svd_batched<T>(h, probs, bsig.get(), bperm.get());
-  // Row phase basis: V1 (n1 x S); U1 packed per block; Sigma1
+  // Row phase basis: V1 (n1 x k0); U1 packed per block (all S); Sigma1
   const int64_t s_row = std::min<int64_t>({(r * n1 + n - 1) / n, S + m2, n1});
   const int64_t cr = chunk_row > 0 ? chunk_row : DEFAULT_CHUNK;
-  const int64_t kmax_r = std::max<int64_t>({S, s_row, 1});
+  // Block triplet g (blocks in order, descending within a block) goes to
+  // state column pos[g].  With several appends the running SVD of Eq. 2 holds
+  // rank s_row between appends and the block SVD is its initial state, so only
+  // the s_row largest block triplets are kept (descending; equal values: lower
+  // index first); with one append all S enter the single merge of Eq. 2.
+  std::vector<int32_t> pos(std::max<int64_t>(S, 1));
+  int64_t k0 = S;
+  {
+    std::vector<double> hsig(std::max<int64_t>(sigtot, 1)), sig_all(std::max<int64_t>(S, 1));
+    if (sigtot > 0) d2h_sync(hsig.data(), bsig.get(), size_t(sigtot) * 8, st);
+    for (const BlkDesc& d : bd)
+      for (int64_t t = 0; t < d.s_b; ++t) sig_all[d.soff + t] = hsig[d.sig_off + t];
+    for (int64_t g = 0; g < S; ++g) pos[g] = int32_t(g);
+    if (cr < m2 && S > s_row) {
+      std::vector<int32_t> idx(S);
+      for (int64_t g = 0; g < S; ++g) idx[g] = int32_t(g);
+      std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return sig_all[a] > sig_all[b]; });
+      k0 = s_row;
+      for (int64_t g = 0; g < S; ++g) pos[g] = -1;
+      for (int64_t j = 0; j < k0; ++j) pos[idx[j]] = int32_t(j);
+    }
+  }
+  const int64_t kmax_r = std::max<int64_t>({k0, s_row, 1});
   Phase<T> rowp(h, std::max<int64_t>(n1, 1), kmax_r, S + m2, std::min(cr, std::max<int64_t>(m2, 1)),
                 sizeof(T) == 8 ? DROP_TOL_FP64 : DROP_TOL_MIXED);
   DArr<T> U1(std::max<int64_t>(utot, 1), st);
   DArr<BlkDesc> d_bd(std::max<int64_t>(blk.B, 1), st);
   if (blk.B > 0) CK(cudaMemcpyAsync(d_bd.get(), bd.data(), sizeof(BlkDesc) * blk.B, cudaMemcpyHostToDevice, st));
-  set_zero<T>(st, n1, S, rowp.U(), kmax_r);
+  set_zero<T>(st, n1, k0, rowp.U(), kmax_r);
+  set_zero<T>(st, S, k0, rowp.Wm(), kmax_r);
   if (S > 0) {
-    // k_block_out writes V1 with leading dimension S; use a staging buffer then copy
-    DArr<T> V1(n1 * S, st);
-    set_zero<T>(st, n1, S, V1.get(), S);
+    DArr<int32_t> d_pos(S, st);
+    CK(cudaMemcpyAsync(d_pos.get(), pos.data(), size_t(S) * 4, cudaMemcpyHostToDevice, st));
     std::vector<BlkDesc> act;
     for (auto& d : bd)
       if (d.s_b > 0) act.push_back(d);
     DArr<BlkDesc> d_act(int64_t(act.size()), st);
     CK(cudaMemcpyAsync(d_act.get(), act.data(), sizeof(BlkDesc) * act.size(), cudaMemcpyHostToDevice, st));
     k_block_out<T><<<unsigned(act.size()), 128, 0, st>>>(d_act.get(), bdata.get(), vbuf.get(), bsig.get(),
-                                                         bperm.get(), S, V1.get(), U1.get(), rowp.S());
+                                                         bperm.get(), d_pos.get(), kmax_r, rowp.U(), U1.get(),
+                                                         rowp.S());
     CK_LAUNCH();
-    copy2d<T, T>(st, n1, S, V1.get(), S, rowp.U(), kmax_r);
+    k_select_w<T><<<g1(S), 256, 0, st>>>(d_pos.get(), S, rowp.Wm(), kmax_r);
+    CK_LAUNCH();
   }
-  set_identity<T>(st, S, S, rowp.Wm(), kmax_r);
-  rowp.k = S;
+  rowp.k = k0;
   rowp.q = S;
   info.ms_block_svd = tm.stop();
 
