@@ -318,7 +318,8 @@ def main():
         e2e = {"value": world * F / statistics.mean(e_times) / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "seconds_per_step": statistics.mean(e_times)}
 
-    # roofline of the dominant kernel (the FP32 Jacobi SVD, ALU-bound)
+    # roofline of the dominant kernel (the FP32 block-Jacobi core SVD, ALU-bound;
+    # flops counted as for scalar one-sided Jacobi: sweeps x n(n-1)/2 pairs x 18 n)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -330,7 +331,7 @@ def main():
     avg_ms = cnt_mixed["jacobi_ms"] / jl
     achieved = (cnt_mixed["jacobi_flops"] / jl) / (avg_ms / 1000.0) / 1e12 if avg_ms > 0 else 0.0
     share = cnt_mixed["jacobi_ms"] / 1000.0 / max(sum(t_mixed), 1e-9)
-    roofline = {"kernel": "k_jacobi<float> (batched one-sided Jacobi SVD)", "bound": "alu",
+    roofline = {"kernel": "k_jacobi_block (block one-sided Jacobi core SVD, FP32)", "bound": "alu",
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                 "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz "
                                                 "(MEASURED_PEAKS.json)", "time_share": share,
@@ -348,8 +349,9 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": cfg.name, "m": m, "n": n, "nnz": int(w["col"].size), "r": cfg.r, "k": cfg.k,
                        "L": int(Yd.shape[1]), "chunk": CHUNK, "gamma": cfg.gamma, "seed": 0,
-                       "precision": "mixed: FP32 storage and FP32 SIMT products, FP64 Gram Cholesky, "
-                                    "FP32 Jacobi core SVD",
+                       "precision": "mixed: FP32 storage, TF32 tensor-core products (split hi/lo, 3 passes) "
+                                    "with FP32 accumulation, FP64-accumulated Gram and FP64 Cholesky, "
+                                    "FP32 block-Jacobi core SVD",
                        "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"},
             "mixed": {"seconds": sec_mixed, "gflops": F / sec_mixed / 1e9, "residual": res_mixed,
                       "stage_ms": {k: info[k] for k in info if k.startswith("ms_")}},

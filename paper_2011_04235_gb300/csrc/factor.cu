@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <type_traits>
 
 #include "dense.cuh"
@@ -725,7 +726,9 @@ struct Phase {
     JacobiStats js;
     bool done = false;
     if constexpr (sizeof(T) == 4) {
-      if (use_cluster_svd) done = jacobi_svd_cluster(h, K.get(), J.get(), int(n), jsig.get(), jperm.get(), &js);
+      done = jacobi_svd_block(h, K.get(), J.get(), int(n), jsig.get(), jperm.get(), &js);
+      if (!done && use_cluster_svd)
+        done = jacobi_svd_cluster(h, K.get(), J.get(), int(n), jsig.get(), jperm.get(), &js);
     }
     if (!done) {
       std::vector<JacobiProblem<T>> pr(1);

@@ -42,4 +42,11 @@ void jacobi_sort_columns(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& pro
 // then uses jacobi_svd_batched.
 bool jacobi_svd_cluster(fastpi_ctx* h, float* K, float* V, int n, double* sig, int32_t* perm, JacobiStats* stats);
 
+// FP32 core SVD of one square n x n column-major K (ld n) by block one-sided
+// Jacobi on the whole GPU (column blocks of 4 or 8 columns; one CTA per block
+// pair and round).  Same outputs as jacobi_svd_cluster; returns false, having
+// done nothing, when a block pair's panels do not fit in one CTA's shared
+// memory or the block pairs of a round exceed the co-resident CTAs.
+bool jacobi_svd_block(fastpi_ctx* h, float* K, float* V, int n, double* sig, int32_t* perm, JacobiStats* stats);
+
 }  // namespace fastpi

@@ -1,0 +1,675 @@
+// Block one-sided Jacobi SVD of one FP32 core matrix on the whole GPU.
+//
+// The scalar one-sided Jacobi of the core K ((k + c) x (k + c), Eqs. 2 / 3)
+// spends its time in n - 1 device- or cluster-wide synchronisations per
+// sweep; the arithmetic per round is tiny.  The block form pairs column
+// BLOCKS instead of columns: with blocks of b = P / 2 columns there are only
+// n / b - 1 rounds per sweep, and everything inside a round is local to one
+// CTA.  CTA w of round rr owns the block pair (I, J) of the circle method and
+//   1. stages the panels X = [K_I K_J] and Y = [V_I V_J] (n x P each) in
+//      shared memory with 16-byte asynchronous copies from L2;
+//   2. forms the Gram matrix G = X^T X (P x P) with register tiles;
+//   3. one warp runs cyclic two-sided Jacobi sweeps on G (the rotation of a
+//      pair comes from G_pp, G_qq, G_pq exactly as from the column dot
+//      products of scalar one-sided Jacobi), accumulating them in Q (P x P);
+//   4. writes K_IJ <- X Q and V_IJ <- Y Q.
+// Every block is owned by exactly one CTA per round, so instead of a
+// device-wide barrier per round a CTA waits only for the two CTAs that wrote
+// its blocks in the previous round: a per-block counter holds the number of
+// rounds completed on that block (release store after the block is written,
+// acquire load before it is read).  A device-wide barrier ends each sweep,
+// where the CTAs combine their rotation flags: a sweep in which no pair had
+// |G_pq| / sqrt(G_pp G_qq) above tol leaves K unchanged (converged), and a
+// sweep whose rotations all stayed below 1e-4 ends the iteration (quadratic
+// convergence leaves the next sweep nothing above tol).
+//
+// K and V are worked on in copies whose leading dimension is a multiple of 4
+// floats (zero rows below n), so every column starts on a 16-byte boundary.
+// Results (the same contract as the other Jacobi kernels): K <- K J with
+// mutually orthogonal columns, V <- J.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include "jacobi.cuh"
+
+namespace fastpi {
+namespace {
+
+constexpr int BT = 512;              // threads per CTA (16 warps)
+constexpr int B_MAX_SWEEPS = 30;
+constexpr int INNER_SWEEPS = 1;      // sweeps of the P x P Gram solve per block pair
+constexpr float B_EARLY_OFF = 1e-4f;
+constexpr unsigned long long B_WAIT_NS = 2000000000ull;   // bound of every wait (2 s)
+
+struct BBar {
+  unsigned count;
+  unsigned gen;
+  int flag[3];
+  double fro2;
+};
+
+__device__ __forceinline__ unsigned long long b_gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned b_ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void b_st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Device-wide barrier of a cooperative launch; false when the bounded wait
+// ran out (status bit set).
+__device__ bool b_barrier(BBar* gb, unsigned* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned gen = b_ld_acquire(&gb->gen);
+    __threadfence();
+    const unsigned arrived = atomicAdd(&gb->count, 1u) + 1u;
+    int ok = 1;
+    if (arrived == gridDim.x) {
+      gb->count = 0;
+      __threadfence();
+      b_st_release(&gb->gen, gen + 1u);
+    } else {
+      const unsigned long long t0 = b_gtimer();
+      unsigned spins = 0;
+      while (b_ld_acquire(&gb->gen) == gen) {
+        if ((++spins & 63u) == 0 && b_gtimer() - t0 > B_WAIT_NS) {
+          atomicOr(status, ST_BARRIER_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ void circle_pair(int slot, int rr, int qe, int& i, int& j) {
+  const int m = qe - 1;
+  if (slot == 0) {
+    i = m;
+    j = rr;
+  } else {
+    i = rr + slot;
+    if (i >= m) i -= m;
+    j = rr - slot;
+    if (j < 0) j += m;
+  }
+  if (i > j) {
+    const int t = i;
+    i = j;
+    j = t;
+  }
+}
+
+// Butterfly reduction of NV per-lane values over the 32 lanes of a warp.
+// NV >= 32: afterwards lane L holds the sums of values [off, off + NV / 32),
+// off built from the lane bits.  NV < 32: lanes that differ only in their
+// lowest log2(32 / NV) bits hold the same single sum, index off.
+template <int NV>
+__device__ __forceinline__ void warp_reduce_scatter(float (&v)[NV], int lane, int& off) {
+  off = 0;
+  int len = NV;
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    if (len > 1) {
+      const int half = len / 2;
+      const bool up = (lane & m) != 0;
+#pragma unroll
+      for (int i = 0; i < NV / 2; ++i) {
+        if (i < half) {
+          const float mine = up ? v[i + half] : v[i];
+          const float other = up ? v[i] : v[i + half];
+          v[i] = mine + __shfl_xor_sync(0xffffffffu, other, m);
+        }
+      }
+      if (up) off += half;
+      len = half;
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], m);
+    }
+  }
+}
+
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// One warp, P <= 8 (the unrolled code of larger P no longer fits the
+// instruction cache): lanes 0..P-1 hold the rows of G, lanes P..2P-1 the rows
+// of Q, in registers; every lane computes all P/2 rotations of a round from
+// shuffled entries of G (the round loop is unrolled, so every column index is
+// a compile-time constant).  Per round: Q <- Q J, G <- J^T G J.
+template <int P>
+__device__ __forceinline__ void inner_solve_regs(const float* G, float* Q, int lane, float tabs, float tol2,
+                                                 float early2, int sweeps, int& rotmax) {
+  constexpr int GS = P + 1;
+  const bool isg = lane < P, isq = lane >= P && lane < 2 * P;
+  const int ri = isg ? lane : (isq ? lane - P : 0);
+  float v[P];
+#pragma unroll
+  for (int c = 0; c < P; ++c) v[c] = isg ? G[ri * GS + c] : ((isq && c == ri) ? 1.f : 0.f);
+  for (int is = 0; is < sweeps; ++is) {
+    int any = 0;
+#pragma unroll
+    for (int ir = 0; ir < P - 1; ++ir) {
+      float cs[P / 2], sn[P / 2];
+#pragma unroll
+      for (int k = 0; k < P / 2; ++k) {
+        int p, q;
+        circle_pair(k, ir, P, p, q);
+        const float al = __shfl_sync(0xffffffffu, v[p], p);
+        const float be = __shfl_sync(0xffffffffu, v[q], q);
+        const float ga = __shfl_sync(0xffffffffu, v[q], p);
+        float c = 1.f, s = 0.f;
+        if (al > tabs && be > tabs && ga * ga > tol2 * al * be) {
+          // t = 2 g sgn(d) / (|d| + sqrt(d^2 + 4 g^2)), d = be - al (smaller root)
+          const float d = be - al;
+          const float h = fmaf(d, d, 4.f * ga * ga);
+          const float t = __fdividef(2.f * (d < 0.f ? -ga : ga), fabsf(d) + h * rsqrtf(h));
+          c = rsqrtf(fmaf(t, t, 1.f));
+          s = c * t;
+          any = 1;
+          rotmax = max(rotmax, ga * ga > early2 * al * be ? 2 : 1);
+        }
+        cs[k] = c;
+        sn[k] = s;
+      }
+      // columns of every row: (x_p, x_q) <- (c x_p - s x_q, s x_p + c x_q)
+#pragma unroll
+      for (int k = 0; k < P / 2; ++k) {
+        int p, q;
+        circle_pair(k, ir, P, p, q);
+        const float x = v[p], y = v[q];
+        v[p] = cs[k] * x - sn[k] * y;
+        v[q] = sn[k] * x + cs[k] * y;
+      }
+      // rows of G: row p <- c row_p - s row_q, row q <- s row_p + c row_q
+      float cc = 1.f, ss = 0.f;
+      int mate = lane;
+#pragma unroll
+      for (int k = 0; k < P / 2; ++k) {
+        int p, q;
+        circle_pair(k, ir, P, p, q);
+        if (isg && ri == p) {
+          cc = cs[k];
+          ss = -sn[k];
+          mate = q;
+        } else if (isg && ri == q) {
+          cc = cs[k];
+          ss = sn[k];
+          mate = p;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < P; ++c) {
+        const float y = __shfl_sync(0xffffffffu, v[c], mate);
+        v[c] = cc * v[c] + ss * y;
+      }
+    }
+    if (!any) break;
+  }
+  if (isq) {
+#pragma unroll
+    for (int c = 0; c < P; ++c) Q[ri * GS + c] = v[c];
+  }
+}
+
+#ifdef FASTPI_PHASE_CLOCKS
+__device__ long long g_phase_clk[8];
+#define PHASE_MARK(k)                          \
+  do {                                         \
+    if (blockIdx.x == gridDim.x / 2 && threadIdx.x == 0) { \
+      const long long t_ = clock64();          \
+      g_phase_clk[k] += t_ - t_mark;           \
+      t_mark = t_;                             \
+    }                                          \
+  } while (0)
+#else
+#define PHASE_MARK(k) \
+  do {                \
+  } while (0)
+#endif
+
+struct BlkArgs {
+  float* K;        // ldk x n column-major: in A (rows >= n zero), out A J
+  float* V;        // ldk x n column-major: in I, out J
+  unsigned* ver;   // [nb] rounds completed per block
+  int n, ldk;      // ldk: multiple of 4, >= n
+  int nb;          // number of column blocks (even; the last may be empty)
+  float tol;
+  int inner;       // sweeps of the P x P Gram solve
+  BBar* gb;
+  int* out;        // [0] sweeps used, [1] hit the sweep cap
+  unsigned* status;
+};
+
+template <int P>
+__global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
+  constexpr int B = P / 2;         // columns per block
+  constexpr int TW = P / 4;        // Gram tile edge (4 x 4 tiles of TW x TW)
+  constexpr int GS = P + 1;        // padded row stride of G and Q
+  extern __shared__ float4 smem4[];
+  const int ldk = a.ldk, n = a.n;
+  float* Xs = reinterpret_cast<float*>(smem4);   // [P][ldk]
+  float* Ys = Xs + size_t(P) * ldk;              // [P][ldk]
+  float* G = Ys + size_t(P) * ldk;               // [P][GS]
+  float* Q = G + P * GS;                         // [P][GS]
+  __shared__ float s_c[P / 2], s_s[P / 2];
+  __shared__ int s_gcol[P];
+  __shared__ int s_rot, s_ok, s_pair_rot;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float tabs = [&] {
+    const float ne = float(n) * 1.1920929e-7f;
+    return float(double(ne) * double(ne) * a.gb->fro2);
+  }();
+  const float tol2 = a.tol * a.tol, early2 = B_EARLY_OFF * B_EARLY_OFF;
+  if (tid == 0) s_rot = 0;
+  const int nq = ldk / 4;   // 16-byte chunks per column
+
+  int sweep = 0;
+#ifdef FASTPI_PHASE_CLOCKS
+  long long t_mark = clock64();
+#endif
+  for (;;) {
+    for (int rr = 0; rr < a.nb - 1; ++rr) {
+      const unsigned t = unsigned(sweep) * unsigned(a.nb - 1) + unsigned(rr);
+      int bi, bj;
+      circle_pair(blockIdx.x, rr, a.nb, bi, bj);
+      if (tid < P) {
+        const int g = tid < B ? bi * B + tid : bj * B + (tid - B);
+        s_gcol[tid] = g < n ? g : -1;
+      }
+      // wait until the previous round on both blocks is complete
+      if (tid == 0) {
+        int ok = 1;
+        if (b_ld_acquire(a.ver + bi) < t || b_ld_acquire(a.ver + bj) < t) {
+          const unsigned long long t0 = b_gtimer();
+          unsigned spins = 0;
+          while (b_ld_acquire(a.ver + bi) < t || b_ld_acquire(a.ver + bj) < t) {
+            if ((++spins & 63u) == 0 && b_gtimer() - t0 > B_WAIT_NS) {
+              atomicOr(a.status, ST_BARRIER_TIMEOUT);
+              ok = 0;
+              break;
+            }
+          }
+        }
+        // the acquire loads order this CTA's reads (through the barrier below)
+        // after the producers' writes
+        s_ok = ok;
+        s_pair_rot = 0;
+      }
+      __syncthreads();
+      if (!s_ok) return;
+      PHASE_MARK(5);
+      // 1. panels: X (first group), Y (second group)
+      for (int e = tid; e < P * nq; e += BT) {
+        const int c = e / nq, r4 = (e - c * nq) * 4;
+        const int g = s_gcol[c];
+        float* d = Xs + size_t(c) * ldk + r4;
+        if (g >= 0)
+          cp_async16(d, a.K + size_t(g) * ldk + r4);
+        else
+          *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      cp_async_commit();
+      for (int e = tid; e < P * nq; e += BT) {
+        const int c = e / nq, r4 = (e - c * nq) * 4;
+        const int g = s_gcol[c];
+        float* d = Ys + size_t(c) * ldk + r4;
+        if (g >= 0)
+          cp_async16(d, a.V + size_t(g) * ldk + r4);
+        else
+          *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      cp_async_commit();
+      cp_async_wait<1>();
+      __syncthreads();
+      PHASE_MARK(0);
+      // 2. Gram: warp w owns tile (w / 4, w % 4); lanes split the rows
+      {
+        const int tp = warp >> 2, tq = warp & 3;
+        float acc[TW * TW];
+#pragma unroll
+        for (int i = 0; i < TW * TW; ++i) acc[i] = 0.f;
+        const float* xa = Xs + size_t(tp * TW) * ldk;
+        const float* xb = Xs + size_t(tq * TW) * ldk;
+#pragma unroll 2
+        for (int r = lane; r < n; r += 32) {
+          float u[TW], w[TW];
+#pragma unroll
+          for (int i = 0; i < TW; ++i) {
+            u[i] = xa[size_t(i) * ldk + r];
+            w[i] = xb[size_t(i) * ldk + r];
+          }
+#pragma unroll
+          for (int i = 0; i < TW; ++i)
+#pragma unroll
+            for (int j = 0; j < TW; ++j) acc[i * TW + j] = fmaf(u[i], w[j], acc[i * TW + j]);
+        }
+        int off;
+        warp_reduce_scatter<TW * TW>(acc, lane, off);
+        if ((TW * TW) >= 32) {
+#pragma unroll
+          for (int e = 0; e < ((TW * TW) >= 32 ? (TW * TW) / 32 : 1); ++e) {
+            const int idx = off + e, i = idx / TW, j = idx % TW;
+            G[(tp * TW + i) * GS + tq * TW + j] = acc[e];
+          }
+        } else if ((lane & (32 / (TW * TW) - 1)) == 0) {
+          const int i = off / TW, j = off % TW;
+          G[(tp * TW + i) * GS + tq * TW + j] = acc[0];
+        }
+      }
+      for (int e = tid; e < P * P; e += BT) Q[(e / P) * GS + e % P] = (e / P == e % P) ? 1.f : 0.f;
+      __syncthreads();
+      PHASE_MARK(1);
+      // 3. one warp: cyclic two-sided Jacobi on G, rotations accumulated in Q
+      if constexpr (P <= 8) {
+        if (warp == 0) {
+          int rotmax = 0;
+          inner_solve_regs<P>(G, Q, lane, tabs, tol2, early2, a.inner, rotmax);
+          if (lane == 0 && rotmax) {
+            atomicMax(&s_rot, rotmax);
+            s_pair_rot = 1;
+          }
+        }
+      } else if (warp == 0) {
+        for (int is = 0; is < a.inner; ++is) {
+          int any = 0;
+          for (int ir = 0; ir < P - 1; ++ir) {
+            if (lane < P / 2) {
+              int p, q;
+              circle_pair(lane, ir, P, p, q);
+              const float al = G[p * GS + p], be = G[q * GS + q], ga = G[p * GS + q];
+              float c = 1.f, s = 0.f;
+              // rotate when |g| / sqrt(al be) > tol (tested without a division)
+              if (al > tabs && be > tabs && ga * ga > tol2 * al * be) {
+                // tan of the angle that zeroes the (p, q) entry, smaller root:
+                // t = 2 g sgn(d) / (|d| + sqrt(d^2 + 4 g^2)), d = be - al
+                const float d = be - al;
+                const float t = 2.f * (d < 0.f ? -ga : ga) / (fabsf(d) + sqrtf(fmaf(d, d, 4.f * ga * ga)));
+                c = rsqrtf(fmaf(t, t, 1.f));
+                s = c * t;
+                any = 1;
+                s_pair_rot = 1;
+                atomicMax(&s_rot, ga * ga > early2 * al * be ? 2 : 1);
+              }
+              s_c[lane] = c;
+              s_s[lane] = s;
+            }
+            __syncwarp();
+            // columns: (x_p, x_q) <- (c x_p - s x_q, s x_p + c x_q) on every
+            // row of G and of Q (rows of G: i < P, rows of Q: P + i)
+            for (int ri = lane; ri < 2 * P; ri += 32) {
+              float* row = ri < P ? G + ri * GS : Q + (ri - P) * GS;
+#pragma unroll
+              for (int k = 0; k < P / 2; ++k) {
+                int p, q;
+                circle_pair(k, ir, P, p, q);
+                const float c = s_c[k], s = s_s[k];
+                const float x = row[p], y = row[q];
+                row[p] = c * x - s * y;
+                row[q] = s * x + c * y;
+              }
+            }
+            __syncwarp();
+            // rows of G: the same rotation from the left
+            for (int j = lane; j < P; j += 32) {
+#pragma unroll
+              for (int k = 0; k < P / 2; ++k) {
+                int p, q;
+                circle_pair(k, ir, P, p, q);
+                const float c = s_c[k], s = s_s[k];
+                const float x = G[p * GS + j], y = G[q * GS + j];
+                G[p * GS + j] = c * x - s * y;
+                G[q * GS + j] = s * x + c * y;
+              }
+            }
+            __syncwarp();
+          }
+          any = __any_sync(0xffffffffu, any);
+          if (!any) break;
+        }
+      }
+      cp_async_wait<0>();
+      __syncthreads();
+      PHASE_MARK(2);
+      // 4. K_IJ <- X Q, V_IJ <- Y Q (one row per thread); nothing to write
+      // when no pair of the block pair rotated (Q = I)
+      for (int r = tid; s_pair_rot && r < n; r += BT) {
+        float x[P], y[P];
+#pragma unroll
+        for (int c = 0; c < P; ++c) {
+          x[c] = Xs[size_t(c) * ldk + r];
+          y[c] = Ys[size_t(c) * ldk + r];
+        }
+#pragma unroll 2
+        for (int j = 0; j < P; ++j) {
+          const int g = s_gcol[j];
+          float u = 0.f, v = 0.f;
+#pragma unroll
+          for (int c = 0; c < P; ++c) {
+            const float qc = Q[c * GS + j];
+            u = fmaf(x[c], qc, u);
+            v = fmaf(y[c], qc, v);
+          }
+          if (g >= 0) {
+            __stcg(a.K + size_t(g) * ldk + r, u);
+            __stcg(a.V + size_t(g) * ldk + r, v);
+          }
+        }
+      }
+      __syncthreads();
+      PHASE_MARK(3);
+      // hand both blocks to the next round (the release store publishes every
+      // write of the CTA, ordered before it by the barrier above)
+      if (tid == 0) {
+        b_st_release(a.ver + bi, t + 1u);
+        b_st_release(a.ver + bj, t + 1u);
+      }
+      if (rr == a.nb - 2) {
+        // end of a sweep: combine the rotation flags of all CTAs
+        if (tid == 0) {
+          atomicMax(&a.gb->flag[sweep % 3], s_rot);
+          if (blockIdx.x == 0) a.gb->flag[(sweep + 1) % 3] = 0;
+        }
+        if (!b_barrier(a.gb, a.status)) return;
+        PHASE_MARK(4);
+        ++sweep;
+        const int any = *(volatile int*)&a.gb->flag[(sweep - 1) % 3];
+        __syncthreads();
+        if (tid == 0) s_rot = 0;
+        if (any < 2 || sweep >= B_MAX_SWEEPS) {
+          if (blockIdx.x == 0 && tid == 0) {
+            a.out[0] = sweep;
+            a.out[1] = any >= 2 ? 1 : 0;
+            if (any >= 2) atomicOr(a.status, ST_JACOBI_SWEEPS);
+          }
+          return;
+        }
+      }
+    }
+  }
+}
+
+// ||K||_F^2 in a fixed order: per-CTA partial sums, then one CTA.
+__global__ void k_b_sumsq_part(const float* __restrict__ K, int64_t len, double* part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < len; i += int64_t(gridDim.x) * blockDim.x) {
+    const double v = K[i];
+    s += v * v;
+  }
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
+}
+__global__ void k_b_sumsq_final(const double* part, int np, BBar* gb) {
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < np; ++i) s += part[i];
+    gb->fro2 = s;
+    gb->count = 0;
+    gb->gen = 0;
+    gb->flag[0] = gb->flag[1] = gb->flag[2] = 0;
+  }
+}
+
+// Kp (ldk x n) <- K (n x n, ld n) with zero rows n..ldk-1; Vp <- I (ldk x n).
+__global__ void k_b_pad_in(const float* __restrict__ K, int n, int ldk, float* __restrict__ Kp,
+                           float* __restrict__ Vp) {
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= int64_t(ldk) * n) return;
+  const int c = int(e / ldk), r = int(e % ldk);
+  Kp[e] = r < n ? K[int64_t(c) * n + r] : 0.f;
+  Vp[e] = r == c ? 1.f : 0.f;
+}
+// K (n x n) <- Kp, V (n x n) <- Vp.
+__global__ void k_b_pad_out(const float* __restrict__ Kp, const float* __restrict__ Vp, int n, int ldk,
+                            float* __restrict__ K, float* __restrict__ V) {
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= int64_t(n) * n) return;
+  const int c = int(e / n), r = int(e % n);
+  K[e] = Kp[int64_t(c) * ldk + r];
+  V[e] = Vp[int64_t(c) * ldk + r];
+}
+
+template <int P>
+size_t block_smem(int ldk) {
+  return (2 * size_t(P) * ldk + 2 * size_t(P) * (P + 1)) * sizeof(float);
+}
+
+template <int P>
+bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats, float* ms_out, int* sweeps) {
+  cudaStream_t st = hc->stream;
+  constexpr int B = P / 2;
+  int nb = (n + B - 1) / B;
+  if (nb & 1) ++nb;
+  if (nb < 2) nb = 2;
+  const int ldk = (n + 3) / 4 * 4;
+  const size_t smem = block_smem<P>(ldk);
+  int max_smem = 0;
+  CK(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, hc->device));
+  if (smem > size_t(max_smem)) return false;
+  CK(cudaFuncSetAttribute(k_jacobi_block<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  int occ = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi_block<P>, BT, smem));
+  const int grid = nb / 2;
+  if (occ < 1 || int64_t(occ) * hc->num_sms < grid) return false;
+
+  DArr<BBar> gb(1, st);
+  constexpr int NPART = 128;
+  DArr<double> part(NPART, st);
+  DArr<int> out(2, st);
+  DArr<unsigned> ver(nb, st);
+  DArr<float> Kp(int64_t(ldk) * n, st), Vp(int64_t(ldk) * n, st);
+  k_b_sumsq_part<<<NPART, 256, 0, st>>>(K, int64_t(n) * n, part.get());
+  CK_LAUNCH();
+  k_b_sumsq_final<<<1, 32, 0, st>>>(part.get(), NPART, gb.get());
+  CK_LAUNCH();
+  k_b_pad_in<<<unsigned((int64_t(ldk) * n + 255) / 256), 256, 0, st>>>(K, n, ldk, Kp.get(), Vp.get());
+  CK_LAUNCH();
+  CK(cudaMemsetAsync(out.get(), 0, 2 * sizeof(int), st));
+  CK(cudaMemsetAsync(ver.get(), 0, nb * sizeof(unsigned), st));
+  CK(cudaMemsetAsync(hc->dstatus.get(), 0, 4, st));
+
+  BlkArgs a;
+  a.K = Kp.get();
+  a.V = Vp.get();
+  a.ver = ver.get();
+  a.n = n;
+  a.ldk = ldk;
+  a.nb = nb;
+  a.tol = float(std::sqrt(double(n)) * 1.1920928955078125e-07);
+  a.inner = INNER_SWEEPS;
+  a.gb = gb.get();
+  a.out = out.get();
+  a.status = hc->dstatus.get();
+  void* args[] = {&a};
+  cudaEvent_t ev0, ev1;
+  CK(cudaEventCreate(&ev0));
+  CK(cudaEventCreate(&ev1));
+  CK(cudaEventRecord(ev0, st));
+  CK(cudaLaunchCooperativeKernel((void*)k_jacobi_block<P>, dim3(grid), dim3(BT), args, smem, st));
+  CK_LAUNCH();
+  CK(cudaEventRecord(ev1, st));
+  k_b_pad_out<<<unsigned((int64_t(n) * n + 255) / 256), 256, 0, st>>>(Kp.get(), Vp.get(), n, ldk, K, V);
+  CK_LAUNCH();
+  int ho[2] = {0, 0};
+  d2h_sync(ho, out.get(), sizeof ho, st);
+  unsigned stat = 0;
+  d2h_sync(&stat, hc->dstatus.get(), 4, st);
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, ev0, ev1));
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  if (stat & ST_BARRIER_TIMEOUT) fail(FASTPI_ERR_NO_CONVERGENCE, "block Jacobi SVD: a device-wide wait timed out");
+#ifdef FASTPI_PHASE_CLOCKS
+  {
+    long long clk[8] = {0};
+    CK(cudaMemcpyFromSymbol(clk, g_phase_clk, sizeof clk));
+    const long long rounds = std::max<long long>(1, int64_t(ho[0]) * (nb - 1));
+    fprintf(stderr,
+            "block P=%d n=%d sweeps=%d ms=%.3f per-round clk: wait %lld load %lld gram %lld inner %lld apply %lld "
+            "sweep-bar %lld\n",
+            P, n, ho[0], ms, clk[5] / rounds, clk[0] / rounds, clk[1] / rounds, clk[2] / rounds, clk[3] / rounds,
+            clk[4] / rounds);
+    const long long z[8] = {0};
+    CK(cudaMemcpyToSymbol(g_phase_clk, z, sizeof z));
+  }
+#endif
+  *ms_out = ms;
+  *sweeps = ho[0];
+  if (stats) {
+    stats->max_sweeps_used = ho[0];
+    stats->hit_cap = (stat & ST_JACOBI_SWEEPS) != 0;
+  }
+  return true;
+}
+
+}  // namespace
+
+bool jacobi_svd_block(fastpi_ctx* hc, float* K, float* V, int n, double* sig, int32_t* perm, JacobiStats* stats) {
+  if (n < 2) return false;
+  float ms = 0;
+  int sweeps = 0;
+  // blocks of 4 columns while one round's block pairs fit on the SMs (the
+  // fastest form: short rounds, register-resident Gram solve), else blocks of 8
+  bool ok = launch_block<8>(hc, K, V, n, stats, &ms, &sweeps);
+  if (!ok) ok = launch_block<16>(hc, K, V, n, stats, &ms, &sweeps);
+  if (!ok) return false;
+  std::vector<JacobiProblem<float>> pr(1);
+  pr[0] = JacobiProblem<float>{K, V, n, n, n, n};
+  jacobi_sort_columns<float>(hc, pr, sig, perm);
+  const double dn = n;
+  note_jacobi(ms, double(sweeps) * (dn * (dn - 1) / 2) * (12 * dn + 6 * dn));
+  return true;
+}
+
+}  // namespace fastpi
