@@ -9,9 +9,11 @@
 //   1. stages the panels X = [K_I K_J] and Y = [V_I V_J] (n x P each) in
 //      shared memory with 16-byte asynchronous copies from L2;
 //   2. forms the Gram matrix G = X^T X (P x P) with register tiles;
-//   3. one warp runs cyclic two-sided Jacobi sweeps on G (the rotation of a
-//      pair comes from G_pp, G_qq, G_pq exactly as from the column dot
-//      products of scalar one-sided Jacobi), accumulating them in Q (P x P);
+//   3. runs one cyclic two-sided Jacobi sweep on G (the rotation of a pair
+//      comes from G_pp, G_qq, G_pq exactly as from the column dot products of
+//      scalar one-sided Jacobi), accumulating the rotations in Q (P x P):
+//      for P = 16 the whole CTA updates G and Q in shared memory, for P = 8
+//      one warp keeps them in registers;
 //   4. writes K_IJ <- X Q and V_IJ <- Y Q.
 // Every block is owned by exactly one CTA per round, so instead of a
 // device-wide barrier per round a CTA waits only for the two CTAs that wrote
@@ -115,6 +117,17 @@ __device__ __forceinline__ void circle_pair(int slot, int rr, int qe, int& i, in
   }
 }
 
+// Partner of column i in round rr of the circle method over qe columns.
+__device__ __forceinline__ int circle_mate(int i, int rr, int qe) {
+  const int m = qe - 1;
+  if (i == m) return rr;
+  if (i == rr) return m;
+  int j = 2 * rr - i;
+  if (j < 0) j += m;
+  if (j >= m) j -= m;
+  return j;
+}
+
 // Butterfly reduction of NV per-lane values over the 32 lanes of a warp.
 // NV >= 32: afterwards lane L holds the sums of values [off, off + NV / 32),
 // off built from the lane bits.  NV < 32: lanes that differ only in their
@@ -153,6 +166,59 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Whole CTA, any P: G and Q in shared memory, double-buffered.  Per round,
+// threads 0..P/2-1 compute the rotations of the round's pairs, then all
+// threads update the P x P entries of G <- J^T G J and Q <- Q J.  Returns
+// the buffer that holds the final Q.  Runs `sweeps` sweeps.
+template <int P>
+__device__ __forceinline__ float* inner_solve_cta(float* G, float* Gn, float* Q, float* Qn, float* sc, float* so,
+                                                  int tid, float tabs, float tol2, float early2, int sweeps,
+                                                  int* s_rot, int* s_pair_rot) {
+  constexpr int GS = P + 1;
+  for (int is = 0; is < sweeps; ++is) {
+    for (int ir = 0; ir < P - 1; ++ir) {
+      if (tid < P / 2) {
+        int p, q;
+        circle_pair(tid, ir, P, p, q);
+        const float al = G[p * GS + p], be = G[q * GS + q], ga = G[p * GS + q];
+        float c = 1.f, s = 0.f;
+        if (al > tabs && be > tabs && ga * ga > tol2 * al * be) {
+          // t = 2 g sgn(d) / (|d| + sqrt(d^2 + 4 g^2)), d = be - al (smaller root)
+          const float d = be - al;
+          const float h = fmaf(d, d, 4.f * ga * ga);
+          const float t = __fdividef(2.f * (d < 0.f ? -ga : ga), fabsf(d) + h * rsqrtf(h));
+          c = rsqrtf(fmaf(t, t, 1.f));
+          s = c * t;
+          *s_pair_rot = 1;
+          atomicMax(s_rot, ga * ga > early2 * al * be ? 2 : 1);
+        }
+        // x_p' = c x_p - s x_q, x_q' = s x_p + c x_q
+        sc[p] = c;
+        so[p] = -s;
+        sc[q] = c;
+        so[q] = s;
+      }
+      __syncthreads();
+      for (int e = tid; e < P * P; e += BT) {
+        const int i = e / P, j = e % P;
+        const int mi = circle_mate(i, ir, P), mj = circle_mate(j, ir, P);
+        const float ci = sc[i], si = so[i], cj = sc[j], sj = so[j];
+        Gn[i * GS + j] = ci * (cj * G[i * GS + j] + sj * G[i * GS + mj]) +
+                         si * (cj * G[mi * GS + j] + sj * G[mi * GS + mj]);
+        Qn[i * GS + j] = cj * Q[i * GS + j] + sj * Q[i * GS + mj];
+      }
+      __syncthreads();
+      float* t = G;
+      G = Gn;
+      Gn = t;
+      t = Q;
+      Q = Qn;
+      Qn = t;
+    }
+  }
+  return Q;
 }
 
 // One warp, P <= 8 (the unrolled code of larger P no longer fits the
@@ -275,7 +341,9 @@ __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
   float* Ys = Xs + size_t(P) * ldk;              // [P][ldk]
   float* G = Ys + size_t(P) * ldk;               // [P][GS]
   float* Q = G + P * GS;                         // [P][GS]
-  __shared__ float s_c[P / 2], s_s[P / 2];
+  float* Gn = Q + P * GS;                        // [P][GS] (second buffers of the Gram solve)
+  float* Qn = Gn + P * GS;                       // [P][GS]
+  __shared__ float s_sc[P], s_so[P];
   __shared__ int s_gcol[P];
   __shared__ int s_rot, s_ok, s_pair_rot;
 
@@ -384,77 +452,24 @@ __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
       for (int e = tid; e < P * P; e += BT) Q[(e / P) * GS + e % P] = (e / P == e % P) ? 1.f : 0.f;
       __syncthreads();
       PHASE_MARK(1);
-      // 3. one warp: cyclic two-sided Jacobi on G, rotations accumulated in Q
+      // 3. cyclic two-sided Jacobi on G, rotations accumulated in Q
+      const float* Qf = Q;
       if constexpr (P <= 8) {
         if (warp == 0) {
           int rotmax = 0;
           inner_solve_regs<P>(G, Q, lane, tabs, tol2, early2, a.inner, rotmax);
-          if (lane == 0 && rotmax) {
+          if (lane == 0 && rotmax) {   // every lane computed every rotation
             atomicMax(&s_rot, rotmax);
             s_pair_rot = 1;
           }
         }
-      } else if (warp == 0) {
-        for (int is = 0; is < a.inner; ++is) {
-          int any = 0;
-          for (int ir = 0; ir < P - 1; ++ir) {
-            if (lane < P / 2) {
-              int p, q;
-              circle_pair(lane, ir, P, p, q);
-              const float al = G[p * GS + p], be = G[q * GS + q], ga = G[p * GS + q];
-              float c = 1.f, s = 0.f;
-              // rotate when |g| / sqrt(al be) > tol (tested without a division)
-              if (al > tabs && be > tabs && ga * ga > tol2 * al * be) {
-                // tan of the angle that zeroes the (p, q) entry, smaller root:
-                // t = 2 g sgn(d) / (|d| + sqrt(d^2 + 4 g^2)), d = be - al
-                const float d = be - al;
-                const float t = 2.f * (d < 0.f ? -ga : ga) / (fabsf(d) + sqrtf(fmaf(d, d, 4.f * ga * ga)));
-                c = rsqrtf(fmaf(t, t, 1.f));
-                s = c * t;
-                any = 1;
-                s_pair_rot = 1;
-                atomicMax(&s_rot, ga * ga > early2 * al * be ? 2 : 1);
-              }
-              s_c[lane] = c;
-              s_s[lane] = s;
-            }
-            __syncwarp();
-            // columns: (x_p, x_q) <- (c x_p - s x_q, s x_p + c x_q) on every
-            // row of G and of Q (rows of G: i < P, rows of Q: P + i)
-            for (int ri = lane; ri < 2 * P; ri += 32) {
-              float* row = ri < P ? G + ri * GS : Q + (ri - P) * GS;
-#pragma unroll
-              for (int k = 0; k < P / 2; ++k) {
-                int p, q;
-                circle_pair(k, ir, P, p, q);
-                const float c = s_c[k], s = s_s[k];
-                const float x = row[p], y = row[q];
-                row[p] = c * x - s * y;
-                row[q] = s * x + c * y;
-              }
-            }
-            __syncwarp();
-            // rows of G: the same rotation from the left
-            for (int j = lane; j < P; j += 32) {
-#pragma unroll
-              for (int k = 0; k < P / 2; ++k) {
-                int p, q;
-                circle_pair(k, ir, P, p, q);
-                const float c = s_c[k], s = s_s[k];
-                const float x = G[p * GS + j], y = G[q * GS + j];
-                G[p * GS + j] = c * x - s * y;
-                G[q * GS + j] = s * x + c * y;
-              }
-            }
-            __syncwarp();
-          }
-          any = __any_sync(0xffffffffu, any);
-          if (!any) break;
-        }
+      } else {
+        Qf = inner_solve_cta<P>(G, Gn, Q, Qn, s_sc, s_so, tid, tabs, tol2, early2, a.inner, &s_rot, &s_pair_rot);
       }
+      PHASE_MARK(2);
       cp_async_wait<0>();
       __syncthreads();
-      PHASE_MARK(2);
+      PHASE_MARK(6);
       // 4. K_IJ <- X Q, V_IJ <- Y Q (one row per thread); nothing to write
       // when no pair of the block pair rotated (Q = I)
       for (int r = tid; s_pair_rot && r < n; r += BT) {
@@ -470,7 +485,7 @@ __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
           float u = 0.f, v = 0.f;
 #pragma unroll
           for (int c = 0; c < P; ++c) {
-            const float qc = Q[c * GS + j];
+            const float qc = Qf[c * GS + j];
             u = fmaf(x[c], qc, u);
             v = fmaf(y[c], qc, v);
           }
@@ -562,7 +577,7 @@ __global__ void k_b_pad_out(const float* __restrict__ Kp, const float* __restric
 
 template <int P>
 size_t block_smem(int ldk) {
-  return (2 * size_t(P) * ldk + 2 * size_t(P) * (P + 1)) * sizeof(float);
+  return (2 * size_t(P) * ldk + 4 * size_t(P) * (P + 1)) * sizeof(float);
 }
 
 template <int P>
@@ -636,10 +651,10 @@ bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats,
     CK(cudaMemcpyFromSymbol(clk, g_phase_clk, sizeof clk));
     const long long rounds = std::max<long long>(1, int64_t(ho[0]) * (nb - 1));
     fprintf(stderr,
-            "block P=%d n=%d sweeps=%d ms=%.3f per-round clk: wait %lld load %lld gram %lld inner %lld apply %lld "
-            "sweep-bar %lld\n",
-            P, n, ho[0], ms, clk[5] / rounds, clk[0] / rounds, clk[1] / rounds, clk[2] / rounds, clk[3] / rounds,
-            clk[4] / rounds);
+            "block P=%d n=%d sweeps=%d ms=%.3f per-round clk: wait %lld load %lld gram %lld inner %lld ywait %lld "
+            "apply %lld sweep-bar %lld\n",
+            P, n, ho[0], ms, clk[5] / rounds, clk[0] / rounds, clk[1] / rounds, clk[2] / rounds, clk[6] / rounds,
+            clk[3] / rounds, clk[4] / rounds);
     const long long z[8] = {0};
     CK(cudaMemcpyToSymbol(g_phase_clk, z, sizeof z));
   }
@@ -659,10 +674,10 @@ bool jacobi_svd_block(fastpi_ctx* hc, float* K, float* V, int n, double* sig, in
   if (n < 2) return false;
   float ms = 0;
   int sweeps = 0;
-  // blocks of 4 columns while one round's block pairs fit on the SMs (the
-  // fastest form: short rounds, register-resident Gram solve), else blocks of 8
-  bool ok = launch_block<8>(hc, K, V, n, stats, &ms, &sweeps);
-  if (!ok) ok = launch_block<16>(hc, K, V, n, stats, &ms, &sweeps);
+  // blocks of 8 columns (16-column panels); blocks of 4 when the panels of 8
+  // do not fit in shared memory but a round's block pairs still fit on the SMs
+  bool ok = launch_block<16>(hc, K, V, n, stats, &ms, &sweeps);
+  if (!ok) ok = launch_block<8>(hc, K, V, n, stats, &ms, &sweeps);
   if (!ok) return false;
   std::vector<JacobiProblem<float>> pr(1);
   pr[0] = JacobiProblem<float>{K, V, n, n, n, n};
