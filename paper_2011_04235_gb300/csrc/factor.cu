@@ -366,40 +366,60 @@ __global__ void k_pchol(const double* G, int c, const double* dn, double tol, do
 // index); when it is <= thr the factorization stops (state[0] = 1).  The
 // panel's columns of Lo are staged in shared memory.
 constexpr int PCHOL_NB = 32;
-__global__ void k_pchol_panel(const double* __restrict__ G, int c, int t0, const double* dn, double tol,
-                              double* d, int32_t* used, double* Lo, int32_t* piv, int32_t* kept, int32_t* state) {
-  extern __shared__ double pan[];   // c x PCHOL_NB: Lo[:, t0 + k]
+constexpr int PCHOL_THREADS = 256;
+__global__ void __launch_bounds__(PCHOL_THREADS) k_pchol_panel(const double* __restrict__ G, int c, int t0,
+                                                               const double* dn, double tol, double* d,
+                                                               int32_t* used, double* Lo, int32_t* piv,
+                                                               int32_t* kept, int32_t* state) {
+  extern __shared__ double pan[];   // c x PCHOL_NB: Lo[:, t0 + k]; then d_s[c]; then used_s[c]
+  double* d_s = pan + size_t(c) * PCHOL_NB;
+  int* used_s = reinterpret_cast<int*>(d_s + c);
+  __shared__ double red_v[PCHOL_THREADS / 32];
+  __shared__ int red_i[PCHOL_THREADS / 32];
   __shared__ double s_best, s_thr;
   __shared__ int s_arg;
-  __shared__ double red_v[32];
-  __shared__ int red_i[32];
   if (state[0]) return;   // an earlier panel stopped the factorization
   const int nb = min(PCHOL_NB, c - t0);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (t0 == 0) {
-    for (int i = threadIdx.x; i < c; i += blockDim.x) {
-      d[i] = G[int64_t(i) * c + i];
-      used[i] = 0;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  constexpr int NW = PCHOL_THREADS / 32;
+  // state of the pivoting (diagonal of the Schur complement, used columns) in
+  // shared memory for the whole panel; the drop threshold from the largest
+  // appended column norm (block reduction)
+  double mx = 0.0;
+  for (int i = tid; i < c; i += PCHOL_THREADS) {
+    if (t0 == 0) {
+      d_s[i] = G[int64_t(i) * c + i];
+      used_s[i] = 0;
       kept[i] = 0;
       piv[i] = -1;
+    } else {
+      d_s[i] = d[i];
+      used_s[i] = used[i];
     }
-    for (int64_t e = threadIdx.x; e < int64_t(c) * c; e += blockDim.x) Lo[e] = 0.0;
+    mx = fmax(mx, dn[i]);
   }
-  for (int e = threadIdx.x; e < c * PCHOL_NB; e += blockDim.x) pan[e] = 0.0;
-  if (threadIdx.x == 0) {
-    double mx = 0;
-    for (int t = 0; t < c; ++t) mx = fmax(mx, dn[t]);
-    s_thr = tol * tol * mx;
+  if (t0 == 0)
+    for (int64_t e = tid; e < int64_t(c) * c; e += PCHOL_THREADS) Lo[e] = 0.0;
+  for (int e = tid; e < c * PCHOL_NB; e += PCHOL_THREADS) pan[e] = 0.0;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) red_v[w] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double m2 = 0.0;
+    for (int q = 0; q < NW; ++q) m2 = fmax(m2, red_v[q]);
+    s_thr = tol * tol * m2;
   }
   __syncthreads();
   int stop = 0;
   for (int k = 0; k < nb; ++k) {
     const int t = t0 + k;
+    // pivot: the unused column with the largest remaining diagonal (ties: lower index)
     double bv = -1.0;
     int bi = c;
-    for (int i = threadIdx.x; i < c; i += blockDim.x)
-      if (!used[i] && (d[i] > bv || (d[i] == bv && i < bi))) {
-        bv = d[i];
+    for (int i = tid; i < c; i += PCHOL_THREADS)
+      if (!used_s[i] && (d_s[i] > bv || (d_s[i] == bv && i < bi))) {
+        bv = d_s[i];
         bi = i;
       }
 #pragma unroll
@@ -416,49 +436,62 @@ __global__ void k_pchol_panel(const double* __restrict__ G, int c, int t0, const
       red_i[w] = bi;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double v = red_v[0];
-      int ii = red_i[0];
-      for (int q = 1; q < nw; ++q)
-        if (red_v[q] > v || (red_v[q] == v && red_i[q] < ii)) {
-          v = red_v[q];
-          ii = red_i[q];
+    if (w == 0) {
+      bv = lane < NW ? red_v[lane] : -1.0;
+      bi = lane < NW ? red_i[lane] : c;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) {
+          bv = ov;
+          bi = oi;
         }
-      s_best = v;
-      s_arg = ii;
+      }
+      if (lane == 0) {
+        s_best = bv;
+        s_arg = bi;
+      }
     }
     __syncthreads();
-    if (!(s_best > s_thr) || s_arg >= c) {
+    const double best = s_best;
+    const int j = s_arg;
+    if (!(best > s_thr) || j >= c) {
       stop = 1;
       break;
     }
-    const int j = s_arg;
-    const double ljj = sqrt(s_best);
-    if (threadIdx.x == 0) {
-      used[j] = 1;
+    const double ljj = sqrt(best);
+    // column t for every unused row other than the pivot: the Schur complement
+    // column of pivot j (row j of G, by symmetry) minus this panel's earlier columns
+    for (int i = tid; i < c; i += PCHOL_THREADS) {
+      if (i == j) {
+        pan[j * PCHOL_NB + k] = ljj;
+        used_s[j] = 1;
+        continue;
+      }
+      if (used_s[i]) continue;
+      double sacc = G[int64_t(j) * c + i];
+      for (int q = 0; q < k; ++q) sacc -= pan[i * PCHOL_NB + q] * pan[j * PCHOL_NB + q];
+      const double lit = sacc / ljj;
+      pan[i * PCHOL_NB + k] = lit;
+      d_s[i] -= lit * lit;
+    }
+    if (tid == 0) {
       piv[t] = j;
       kept[t] = 1;
-      pan[j * PCHOL_NB + k] = ljj;
       state[1] = t + 1;   // rank so far
     }
     __syncthreads();
-    // column t for every unused row: the Schur complement column of pivot j
-    // (row j of G, by symmetry) minus this panel's earlier columns
-    for (int i = threadIdx.x; i < c; i += blockDim.x) {
-      if (used[i]) continue;
-      double s = G[int64_t(j) * c + i];
-      for (int q = 0; q < k; ++q) s -= pan[i * PCHOL_NB + q] * pan[j * PCHOL_NB + q];
-      const double lit = s / ljj;
-      pan[i * PCHOL_NB + k] = lit;
-      d[i] -= lit * lit;
-    }
-    __syncthreads();
   }
-  for (int e = threadIdx.x; e < c * nb; e += blockDim.x) {
+  for (int e = tid; e < c * nb; e += PCHOL_THREADS) {
     const int i = e / nb, k = e % nb;
     Lo[int64_t(i) * c + t0 + k] = pan[i * PCHOL_NB + k];
   }
-  if (threadIdx.x == 0 && stop) state[0] = 1;
+  for (int i = tid; i < c; i += PCHOL_THREADS) {
+    d[i] = d_s[i];
+    used[i] = used_s[i];
+  }
+  if (tid == 0 && stop) state[0] = 1;
 }
 
 // Lp[a, b] = Lo[piv[a], b] for b <= a < rank (zero elsewhere); rank = state[1].
@@ -666,7 +699,7 @@ struct Phase {
       }
     };
     gram(D.get(), G.get());
-    const size_t pan_bytes = size_t(c) * PCHOL_NB * sizeof(double);
+    const size_t pan_bytes = size_t(c) * PCHOL_NB * sizeof(double) + size_t(c) * (sizeof(double) + sizeof(int));
     if (pan_bytes <= 200 * 1024) {
       // blocked: panels of PCHOL_NB columns in one CTA, trailing updates as FP64 GEMMs
       DArr<double> dd(c, st);
@@ -675,7 +708,7 @@ struct Phase {
       if (pan_bytes > 48 * 1024)
         CK(cudaFuncSetAttribute(k_pchol_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pan_bytes)));
       for (int64_t t0 = 0; t0 < c; t0 += PCHOL_NB) {
-        k_pchol_panel<<<1, 1024, pan_bytes, st>>>(G.get(), int(c), int(t0), dn.get(), drop_tol, dd.get(),
+        k_pchol_panel<<<1, PCHOL_THREADS, pan_bytes, st>>>(G.get(), int(c), int(t0), dn.get(), drop_tol, dd.get(),
                                                   used.get(), Lo.get(), piv.get(), kept.get(), pstate.get());
         CK_LAUNCH();
         const int64_t nbp = std::min<int64_t>(PCHOL_NB, c - t0);
