@@ -157,7 +157,16 @@ fastpi_status fastpi_residual_noalloc(int64_t m, int64_t n, const int64_t* rowpt
                                       const double* val, const double* Y, int64_t L, int64_t ldy,
                                       const double* Z, int64_t ldz, double* out, void* cuda_stream);
 
-/* Getters (valid after fastpi_factor; FASTPI_ERR_STATE before). */
+/* Algorithm 2 (Section 3.2) alone: the hub-and-spoke reordering of A for hub
+ * ratio k in (0, 1), without any factorization.  Afterwards fastpi_get_perm,
+ * fastpi_get_blocks and fastpi_get_info (reordering fields; the factorization
+ * fields are zero) are valid and the factor getters return FASTPI_ERR_STATE
+ * until fastpi_factor runs.  Gives the same permutation as fastpi_factor with
+ * the same k.  Errors: FASTPI_ERR_ARG (k outside (0, 1)), FASTPI_ERR_CUDA. */
+fastpi_status fastpi_reorder(fastpi_t h, double k);
+
+/* Getters (valid after fastpi_factor; FASTPI_ERR_STATE before; fastpi_get_perm,
+ * fastpi_get_blocks and fastpi_get_info also after fastpi_reorder). */
 fastpi_status fastpi_get_rank(fastpi_t h, int64_t* r_out);            /* host int64 */
 fastpi_status fastpi_get_S(fastpi_t h, double* S);                    /* host float64[r'], descending */
 /* U: device float64 m x r' row-major (ldu >= r'), rows in ORIGINAL order. */

@@ -39,6 +39,9 @@ void require(bool ok, fastpi_status s, const char* msg) {
 }
 
 void require_factored(fastpi_t h) { require(h->factored && h->fac, FASTPI_ERR_STATE, "call fastpi_factor first"); }
+void require_reordered(fastpi_t h) {
+  require(h->reordered && h->fac, FASTPI_ERR_STATE, "call fastpi_reorder or fastpi_factor first");
+}
 
 void use_device(fastpi_t h) { CK(cudaSetDevice(h->device)); }
 
@@ -109,7 +112,19 @@ fastpi_status fastpi_factor(fastpi_t h, int64_t r, double k, fastpi_precision pr
   require(prec == FASTPI_FP64 || prec == FASTPI_MIXED_TF32, FASTPI_ERR_ARG, "unknown precision");
   require(chunk_row >= 0 && chunk_col >= 0, FASTPI_ERR_ARG, "chunk sizes must be >= 0");
   h->factored = false;
+  h->reordered = false;
   fastpi::factor(h, r, k, prec, chunk_row, chunk_col);
+  API_END(h)
+}
+
+fastpi_status fastpi_reorder(fastpi_t h, double k) {
+  if (!h) return FASTPI_ERR_ARG;
+  API_BEGIN
+  use_device(h);
+  require(k > 0.0 && k < 1.0 && std::isfinite(k), FASTPI_ERR_ARG, "hub ratio k must lie in (0, 1)");
+  h->factored = false;
+  h->reordered = false;
+  fastpi::reorder_only(h, k);
   API_END(h)
 }
 
@@ -220,7 +235,7 @@ fastpi_status fastpi_get_perm(fastpi_t h, int32_t* row_order, int32_t* col_order
   if (!h) return FASTPI_ERR_ARG;
   API_BEGIN
   use_device(h);
-  require_factored(h);
+  require_reordered(h);
   const Reordering& R = h->fac->R;
   cudaStream_t st = h->stream;
   if (row_order) CK(cudaMemcpyAsync(row_order, R.row_order.get(), size_t(R.m) * 4, cudaMemcpyDeviceToHost, st));
@@ -234,7 +249,7 @@ fastpi_status fastpi_get_perm(fastpi_t h, int32_t* row_order, int32_t* col_order
 fastpi_status fastpi_get_blocks(fastpi_t h, int64_t* B, int64_t* row_off, int64_t* col_off) {
   if (!h) return FASTPI_ERR_ARG;
   API_BEGIN
-  require_factored(h);
+  require_reordered(h);
   const Reordering& R = h->fac->R;
   if (B) *B = R.num_blocks;
   if (row_off) std::memcpy(row_off, R.row_off.data(), R.row_off.size() * 8);
@@ -245,7 +260,7 @@ fastpi_status fastpi_get_blocks(fastpi_t h, int64_t* B, int64_t* row_off, int64_
 fastpi_status fastpi_get_info(fastpi_t h, fastpi_info* info) {
   if (!h) return FASTPI_ERR_ARG;
   API_BEGIN
-  require_factored(h);
+  require_reordered(h);
   require(info != nullptr, FASTPI_ERR_ARG, "info is NULL");
   *info = h->info;
   API_END(h)

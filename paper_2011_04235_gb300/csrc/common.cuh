@@ -82,6 +82,7 @@ struct fastpi_ctx {
   fastpi::DArr<unsigned> dstatus;   // device status word
   // results
   bool factored = false;
+  bool reordered = false;   // fac->R holds Algorithm 2's result (after fastpi_reorder or fastpi_factor)
   fastpi::Factors* fac = nullptr;
   fastpi_info info{};
   std::string last_error;

@@ -576,6 +576,31 @@ __global__ void k_core_vectors(int64_t n, int64_t kk, const T* __restrict__ Kb, 
   Vt[e] = J[src * n + i];
 }
 
+// G <- (3 I - G) / 2 for a cols x cols matrix (one Newton-Schulz coefficient).
+__global__ void k_ns_coef(float* G, int64_t cols) {
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= cols * cols) return;
+  const int64_t i = e / cols, j = e % cols;
+  G[e] = (i == j ? 1.5f : 0.f) - 0.5f * G[e];
+}
+
+// One Newton-Schulz step towards the nearest matrix with orthonormal columns,
+// X <- X (3 I - X^T X) / 2, for X rows x cols (row-major, ld cols) in FP32.
+// The FP32 core SVD's V is a product of thousands of FP32 rotations per
+// column, orthonormal to ~1e-5 per core; the incremental update multiplies
+// these factors into the basis append after append, so without this step the
+// deviation of U^T U and V^T V from I grows with the number of appends.  One
+// step brings it to the rounding level of the products (~1e-6).
+void ns_orthonormalize(cudaStream_t st, int64_t rows, int64_t cols, float* X) {
+  if (rows <= 0 || cols <= 0) return;
+  DArr<float> G(cols * cols, st), Y(rows * cols, st);
+  gemm_f32(st, true, false, cols, cols, rows, 1.f, X, cols, X, cols, 0.f, G.get(), cols);
+  k_ns_coef<<<g1(cols * cols), 256, 0, st>>>(G.get(), cols);
+  CK_LAUNCH();
+  gemm_f32(st, false, false, rows, cols, cols, 1.f, X, cols, G.get(), cols, 0.f, Y.get(), cols);
+  CK(cudaMemcpyAsync(X, Y.get(), size_t(rows * cols) * sizeof(float), cudaMemcpyDeviceToDevice, st));
+}
+
 // Single-CTA descending sort of sig[0..k) (ties: lower index first) -> perm.
 __global__ void k_sort_desc(const double* sig, int k, int nq, int32_t* perm, double* sorted) {
   extern __shared__ unsigned char sm[];
@@ -795,6 +820,10 @@ struct Phase {
       k_core_vectors<T><<<g1(n * kk), 256, 0, st>>>(n, kk, K.get(), J.get(), jsig.get(), jperm.get(), Ut.get(),
                                                      Vt.get());
       CK_LAUNCH();
+      if constexpr (sizeof(T) == 4) {
+        ns_orthonormalize(st, n, kk, Ut.get());
+        ns_orthonormalize(st, n, kk, Vt.get());
+      }
     }
     const int nx = cur ^ 1;
     T* Unew = Uc[nx].get();
@@ -1157,6 +1186,35 @@ void factor(fastpi_ctx* h, int64_t r, double k, fastpi_precision prec, int64_t c
   delete h->fac;
   h->fac = F;
   h->factored = true;
+  h->reordered = true;
+}
+
+void reorder_only(fastpi_ctx* h, double k) {
+  Factors* F = new Factors();
+  h->info = fastpi_info{};
+  try {
+    Timer tm(h->stream);
+    tm.start();
+    run_reorder(h, k, F->R);
+    h->info.ms_reorder = tm.stop();
+  } catch (...) {
+    delete F;
+    throw;
+  }
+  const Reordering& R = F->R;
+  h->info.m = h->m;
+  h->info.n = h->n;
+  h->info.nnz = h->nnz;
+  h->info.m1 = R.m1;
+  h->info.n1 = R.n1;
+  h->info.m2 = h->m - R.m1;
+  h->info.n2 = h->n - R.n1;
+  h->info.num_blocks = R.num_blocks;
+  h->info.iterations = R.iterations;
+  delete h->fac;
+  h->fac = F;
+  h->factored = false;
+  h->reordered = true;
 }
 
 void apply_dense(fastpi_ctx* h, const double* Y, int64_t L, int64_t ldy, double* Z, int64_t ldz) {

@@ -18,6 +18,8 @@ struct Factors {
 };
 
 void factor(fastpi_ctx* h, int64_t r, double k, fastpi_precision prec, int64_t chunk_row, int64_t chunk_col);
+// Algorithm 2 alone: the reordering is kept for the permutation / block getters.
+void reorder_only(fastpi_ctx* h, double k);
 void apply_dense(fastpi_ctx* h, const double* Y, int64_t L, int64_t ldy, double* Z, int64_t ldz);
 void apply_csr(fastpi_ctx* h, int64_t L, int64_t nnz_y, const int64_t* yrowptr, const int32_t* ycol,
                const double* yval, double* Z, int64_t ldz);

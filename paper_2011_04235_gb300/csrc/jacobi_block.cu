@@ -187,9 +187,11 @@ __device__ __forceinline__ float* inner_solve_cta(float* G, float* Gn, float* Q,
         if (al > tabs && be > tabs && ga * ga > tol2 * al * be) {
           // t = 2 g sgn(d) / (|d| + sqrt(d^2 + 4 g^2)), d = be - al (smaller root)
           const float d = be - al;
-          const float h = fmaf(d, d, 4.f * ga * ga);
-          const float t = __fdividef(2.f * (d < 0.f ? -ga : ga), fabsf(d) + h * rsqrtf(h));
-          c = rsqrtf(fmaf(t, t, 1.f));
+          // IEEE square root and division: an approximate c (c^2 + s^2 != 1 by a
+          // few ulp with a fixed sign) would scale V's columns a little on every
+          // one of the thousands of rotations each column receives
+          const float t = 2.f * (d < 0.f ? -ga : ga) / (fabsf(d) + sqrtf(fmaf(d, d, 4.f * ga * ga)));
+          c = 1.f / sqrtf(fmaf(t, t, 1.f));
           s = c * t;
           *s_pair_rot = 1;
           atomicMax(s_rot, ga * ga > early2 * al * be ? 2 : 1);
@@ -251,9 +253,11 @@ __device__ __forceinline__ void inner_solve_regs(const float* G, float* Q, int l
         if (al > tabs && be > tabs && ga * ga > tol2 * al * be) {
           // t = 2 g sgn(d) / (|d| + sqrt(d^2 + 4 g^2)), d = be - al (smaller root)
           const float d = be - al;
-          const float h = fmaf(d, d, 4.f * ga * ga);
-          const float t = __fdividef(2.f * (d < 0.f ? -ga : ga), fabsf(d) + h * rsqrtf(h));
-          c = rsqrtf(fmaf(t, t, 1.f));
+          // IEEE square root and division: an approximate c (c^2 + s^2 != 1 by a
+          // few ulp with a fixed sign) would scale V's columns a little on every
+          // one of the thousands of rotations each column receives
+          const float t = 2.f * (d < 0.f ? -ga : ga) / (fabsf(d) + sqrtf(fmaf(d, d, 4.f * ga * ga)));
+          c = 1.f / sqrtf(fmaf(t, t, 1.f));
           s = c * t;
           any = 1;
           rotmax = max(rotmax, ga * ga > early2 * al * be ? 2 : 1);

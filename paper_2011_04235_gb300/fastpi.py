@@ -25,7 +25,7 @@ STATUS = {0: "FASTPI_OK", 1: "FASTPI_ERR_ARG", 2: "FASTPI_ERR_CSR", 3: "FASTPI_E
           5: "FASTPI_ERR_NO_CONVERGENCE", 6: "FASTPI_ERR_STATE"}
 
 # every symbol the header declares
-SYMBOLS = ["fastpi_create", "fastpi_factor", "fastpi_apply", "fastpi_apply_host", "fastpi_apply_csr",
+SYMBOLS = ["fastpi_create", "fastpi_factor", "fastpi_reorder", "fastpi_apply", "fastpi_apply_host", "fastpi_apply_csr",
            "fastpi_residual", "fastpi_residual_noalloc", "fastpi_get_rank", "fastpi_get_S", "fastpi_get_U",
            "fastpi_get_V",
            "fastpi_get_perm", "fastpi_get_blocks", "fastpi_get_info", "fastpi_get_counters",
@@ -107,6 +107,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     sig = {
         "fastpi_create": ([C.POINTER(p), i64, i64, i64, vp, vp, vp, i32, vp], i32),
         "fastpi_factor": ([p, i64, dbl, i32, i64, i64], i32),
+        "fastpi_reorder": ([p, dbl], i32),
         "fastpi_apply": ([p, vp, i64, i64, vp, i64], i32),
         "fastpi_apply_host": ([p, vp, i64, i64, vp, i64], i32),
         "fastpi_apply_csr": ([p, i64, i64, vp, vp, vp, vp, i64], i32),
@@ -200,6 +201,12 @@ class FastPI:
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         with torch.cuda.device(self.device):
             _check(lib().fastpi_factor(self._h, int(r), float(k), prec, int(chunk_row), int(chunk_col)), self._h)
+        return self
+
+    def reorder(self, k: float):
+        """Algorithm 2 alone (perm / blocks / info getters valid afterwards)."""
+        with torch.cuda.device(self.device):
+            _check(lib().fastpi_reorder(self._h, float(k)), self._h)
         return self
 
     def apply(self, Y: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
