@@ -157,6 +157,23 @@ fastpi_status fastpi_residual_noalloc(int64_t m, int64_t n, const int64_t* rowpt
                                       const double* val, const double* Y, int64_t L, int64_t ldy,
                                       const double* Z, int64_t ldz, double* out, void* cuda_stream);
 
+/* Many independent factorizations (Algorithm 1, lines 1-4, once per handle):
+ * handle i is factored at target rank r[i] with the common hub ratio k,
+ * precision and chunk sizes, exactly as fastpi_factor would (same results).
+ * The A11 block SVDs (Eq. 1) of ALL handles run in one persistent batched
+ * launch; the reorderings and the incremental updates of different handles
+ * run concurrently, one host thread per handle, at most `concurrency` (<= 0:
+ * 4) of them in those stages at a time.  Requirements: count >= 1 distinct
+ * handles created on one device; give each handle its own stream, or they
+ * serialise.  The call returns when every factorization has finished (or
+ * failed): FASTPI_OK, or the status of the first failing handle (its message
+ * in fastpi_last_error of that handle, and of NULL); status_out (host,
+ * count entries, may be NULL) receives each handle's status.  Argument errors
+ * (FASTPI_ERR_ARG) are reported before any work starts. */
+fastpi_status fastpi_factor_batched(fastpi_t* hs, int count, const int64_t* r, double k, fastpi_precision prec,
+                                    int64_t chunk_row, int64_t chunk_col, int concurrency,
+                                    fastpi_status* status_out);
+
 /* Algorithm 2 (Section 3.2) alone: the hub-and-spoke reordering of A for hub
  * ratio k in (0, 1), without any factorization.  Afterwards fastpi_get_perm,
  * fastpi_get_blocks and fastpi_get_info (reordering fields; the factorization

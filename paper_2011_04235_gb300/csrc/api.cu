@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "dense.cuh"
 #include "factor.cuh"
@@ -115,6 +116,48 @@ fastpi_status fastpi_factor(fastpi_t h, int64_t r, double k, fastpi_precision pr
   h->reordered = false;
   fastpi::factor(h, r, k, prec, chunk_row, chunk_col);
   API_END(h)
+}
+
+fastpi_status fastpi_factor_batched(fastpi_t* hs, int count, const int64_t* r, double k, fastpi_precision prec,
+                                    int64_t chunk_row, int64_t chunk_col, int concurrency,
+                                    fastpi_status* status_out) {
+  try {
+    require(hs != nullptr && r != nullptr && count >= 1, FASTPI_ERR_ARG, "need count >= 1 handles and ranks");
+    require(k > 0.0 && k < 1.0 && std::isfinite(k), FASTPI_ERR_ARG, "hub ratio k must lie in (0, 1)");
+    require(prec == FASTPI_FP64 || prec == FASTPI_MIXED_TF32, FASTPI_ERR_ARG, "unknown precision");
+    require(chunk_row >= 0 && chunk_col >= 0, FASTPI_ERR_ARG, "chunk sizes must be >= 0");
+    for (int i = 0; i < count; ++i) {
+      require(hs[i] != nullptr, FASTPI_ERR_ARG, "null handle in the batch");
+      require(r[i] >= 1, FASTPI_ERR_ARG, "every target rank must be >= 1");
+      require(hs[i]->device == hs[0]->device, FASTPI_ERR_ARG, "all handles of a batch must be on one device");
+      for (int j = 0; j < i; ++j) require(hs[j] != hs[i], FASTPI_ERR_ARG, "a handle appears twice in the batch");
+    }
+  } catch (const Error& e) {
+    g_create_error = e.msg;
+    return e.status;
+  }
+  std::vector<fastpi_status> st(count, FASTPI_OK);
+  std::vector<std::string> msg(count);
+  try {
+    CK(cudaSetDevice(hs[0]->device));
+    fastpi::factor_batched(hs, count, r, k, prec, chunk_row, chunk_col, concurrency > 0 ? concurrency : 4,
+                           st.data(), msg.data());
+  } catch (const Error& e) {
+    g_create_error = e.msg;
+    return e.status;
+  }
+  fastpi_status first = FASTPI_OK;
+  for (int i = 0; i < count; ++i) {
+    if (status_out) status_out[i] = st[i];
+    if (st[i] != FASTPI_OK) {
+      hs[i]->last_error = msg[i];
+      if (first == FASTPI_OK) {
+        first = st[i];
+        g_create_error = "batch member " + std::to_string(i) + ": " + msg[i];
+      }
+    }
+  }
+  return first;
 }
 
 fastpi_status fastpi_reorder(fastpi_t h, double k) {

@@ -103,6 +103,12 @@ void radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits, cudaS
 // Number of bits needed to represent values in [0, maxval].
 int bits_for(uint64_t maxval);
 
+// Lets `func` launch with up to the device's opt-in maximum of dynamic shared
+// memory.  The attribute belongs to the function for the whole process, so it
+// is always raised to the maximum, never set to one launch's size (a
+// concurrent launch from another host thread could be left below its need).
+void allow_max_dynamic_smem(const void* func);
+
 // Copy device->host of a small POD value / array on the stream and wait.
 void d2h_sync(void* dst, const void* src, size_t bytes, cudaStream_t st);
 

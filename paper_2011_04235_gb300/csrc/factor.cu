@@ -20,6 +20,11 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <functional>
+#include <string>
+#include <thread>
+#include <mutex>
+#include <condition_variable>
 #include <type_traits>
 
 #include "dense.cuh"
@@ -711,7 +716,7 @@ struct Phase {
       using E = std::remove_pointer_t<decltype(L)>;
       const size_t sm = size_t(c) * sizeof(E);
       if (sm > 48 * 1024)
-        CK(cudaFuncSetAttribute(k_trinv_cols<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+        allow_max_dynamic_smem((const void*)k_trinv_cols<E>);
       k_trinv_cols<E><<<unsigned(c), 32, sm, st>>>(L, int(c), kp, Xo);
       CK_LAUNCH();
     };
@@ -731,7 +736,7 @@ struct Phase {
       DArr<int32_t> used(c, st), pstate(2, st);
       CK(cudaMemsetAsync(pstate.get(), 0, 8, st));
       if (pan_bytes > 48 * 1024)
-        CK(cudaFuncSetAttribute(k_pchol_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pan_bytes)));
+        allow_max_dynamic_smem((const void*)k_pchol_panel);
       for (int64_t t0 = 0; t0 < c; t0 += PCHOL_NB) {
         k_pchol_panel<<<1, PCHOL_THREADS, pan_bytes, st>>>(G.get(), int(c), int(t0), dn.get(), drop_tol, dd.get(),
                                                   used.get(), Lo.get(), piv.get(), kept.get(), pstate.get());
@@ -758,7 +763,7 @@ struct Phase {
     const size_t packed = size_t(c) * (c + 1) / 2 * sizeof(T);
     if (packed <= 200 * 1024) {
       if (packed > 48 * 1024)
-        CK(cudaFuncSetAttribute(k_chol_drop_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(packed)));
+        allow_max_dynamic_smem((const void*)k_chol_drop_smem<T>);
       k_chol_drop_smem<T><<<1, 1024, packed, st>>>(GT.get(), int(c), DROP_ABS_PASS2, kept2.get(), rk.get() + 1);
       CK_LAUNCH();
     } else {
@@ -849,7 +854,7 @@ struct Phase {
     DArr<int32_t> perm(k, st);
     DArr<double> sorted(k, st);
     size_t smem = size_t(nq) * 12;
-    if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_sort_desc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    if (smem > 48 * 1024) allow_max_dynamic_smem((const void*)k_sort_desc);
     k_sort_desc<<<1, 1024, smem, st>>>(S(), int(k), nq, perm.get(), sorted.get());
     CK_LAUNCH();
     const int nx = cur ^ 1;
@@ -894,8 +899,16 @@ struct Timer {
   }
 };
 
+// The batched SVD of the A11 blocks (Eq. 1) is a parameter: one instance runs
+// it on its own problems; a batch of instances hands them to a rendezvous that
+// runs one launch over the blocks of every instance.  block_svd(probs, sig,
+// perm) may redirect sig / perm to where it wrote the results.
 template <typename T>
-void factor_impl(fastpi_ctx* h, Factors& F, int64_t r, double kratio, int64_t chunk_row, int64_t chunk_col) {
+using BlockSvdFn = std::function<JacobiStats(const std::vector<JacobiProblem<T>>&, double*&, int32_t*&)>;
+
+template <typename T>
+void factor_impl(fastpi_ctx* h, Factors& F, int64_t r, double kratio, int64_t chunk_row, int64_t chunk_col,
+                 const BlockSvdFn<T>& block_svd) {
   cudaStream_t st = h->stream;
   const int64_t m = h->m, n = h->n;
   fastpi_info& info = h->info;
@@ -953,9 +966,11 @@ void factor_impl(fastpi_ctx* h, Factors& F, int64_t r, double kratio, int64_t ch
     int64_t p = std::max(d.m_b, d.n_b), q = std::min(d.m_b, d.n_b);
     probs.push_back(JacobiProblem<T>{bdata.get() + d.data_off, vbuf.get() + d.v_off, p, q, int(p), int(q)});
   }
-  DArr<double> bsig(std::max<int64_t>(sigtot, 1), st);
-  DArr<int32_t> bperm(std::max<int64_t>(sigtot, 1), st);
-  JacobiStats bjs = jacobi_svd_batched<T>(h, probs, bsig.get(), bperm.get());
+  DArr<double> bsig_own(std::max<int64_t>(sigtot, 1), st);
+  DArr<int32_t> bperm_own(std::max<int64_t>(sigtot, 1), st);
+  double* bsig = bsig_own.get();
+  int32_t* bperm = bperm_own.get();
+  JacobiStats bjs = block_svd(probs, bsig, bperm);
   // Row phase basis: V1 (n1 x k0); U1 packed per block (all S); Sigma1
   const int64_t s_row = std::min<int64_t>({(r * n1 + n - 1) / n, S + m2, n1});
   const int64_t cr = chunk_row > 0 ? chunk_row : DEFAULT_CHUNK;
@@ -968,7 +983,7 @@ void factor_impl(fastpi_ctx* h, Factors& F, int64_t r, double kratio, int64_t ch
   int64_t k0 = S;
   {
     std::vector<double> hsig(std::max<int64_t>(sigtot, 1)), sig_all(std::max<int64_t>(S, 1));
-    if (sigtot > 0) d2h_sync(hsig.data(), bsig.get(), size_t(sigtot) * 8, st);
+    if (sigtot > 0) d2h_sync(hsig.data(), bsig, size_t(sigtot) * 8, st);
     for (const BlkDesc& d : bd)
       for (int64_t t = 0; t < d.s_b; ++t) sig_all[d.soff + t] = hsig[d.sig_off + t];
     for (int64_t g = 0; g < S; ++g) pos[g] = int32_t(g);
@@ -997,8 +1012,8 @@ void factor_impl(fastpi_ctx* h, Factors& F, int64_t r, double kratio, int64_t ch
       if (d.s_b > 0) act.push_back(d);
     DArr<BlkDesc> d_act(int64_t(act.size()), st);
     CK(cudaMemcpyAsync(d_act.get(), act.data(), sizeof(BlkDesc) * act.size(), cudaMemcpyHostToDevice, st));
-    k_block_out<T><<<unsigned(act.size()), 128, 0, st>>>(d_act.get(), bdata.get(), vbuf.get(), bsig.get(),
-                                                         bperm.get(), d_pos.get(), kmax_r, rowp.U(), U1.get(),
+    k_block_out<T><<<unsigned(act.size()), 128, 0, st>>>(d_act.get(), bdata.get(), vbuf.get(), bsig,
+                                                         bperm, d_pos.get(), kmax_r, rowp.U(), U1.get(),
                                                          rowp.S());
     CK_LAUNCH();
     k_select_w<T><<<g1(S), 256, 0, st>>>(d_pos.get(), S, rowp.Wm(), kmax_r);
@@ -1161,6 +1176,13 @@ __global__ void k_sum(const double* x, int64_t n, double* out) {
   }
 }
 
+template <typename T>
+BlockSvdFn<T> own_block_svd(fastpi_ctx* h) {
+  return [h](const std::vector<JacobiProblem<T>>& probs, double*& sig, int32_t*& perm) {
+    return jacobi_svd_batched<T>(h, probs, sig, perm);
+  };
+}
+
 double pinv_tau(const Factors& F) {
   if (F.S.empty()) return 0.0;
   double s1 = *std::max_element(F.S.begin(), F.S.end());
@@ -1169,16 +1191,19 @@ double pinv_tau(const Factors& F) {
 
 }  // namespace
 
-void factor(fastpi_ctx* h, int64_t r, double k, fastpi_precision prec, int64_t chunk_row, int64_t chunk_col) {
+namespace {
+
+template <typename T>
+void factor_into(fastpi_ctx* h, int64_t r, double k, fastpi_precision prec, int64_t chunk_row, int64_t chunk_col,
+                 const BlockSvdFn<T>& block_svd) {
   Factors* F = new Factors();
   F->prec = int(prec);
   h->info = fastpi_info{};
   h->info.precision = int(prec);
+  h->factored = false;
+  h->reordered = false;
   try {
-    if (prec == FASTPI_FP64)
-      factor_impl<double>(h, *F, r, k, chunk_row, chunk_col);
-    else
-      factor_impl<float>(h, *F, r, k, chunk_row, chunk_col);
+    factor_impl<T>(h, *F, r, k, chunk_row, chunk_col, block_svd);
   } catch (...) {
     delete F;
     throw;
@@ -1187,6 +1212,183 @@ void factor(fastpi_ctx* h, int64_t r, double k, fastpi_precision prec, int64_t c
   h->fac = F;
   h->factored = true;
   h->reordered = true;
+}
+
+// Counting semaphore (bounds how many instances of a batch are in a
+// GPU-heavy stage at once).
+class Gate {
+ public:
+  explicit Gate(int n) : free_(n > 0 ? n : 1) {}
+  void acquire() {
+    std::unique_lock<std::mutex> lk(mu_);
+    cv_.wait(lk, [&] { return free_ > 0; });
+    --free_;
+  }
+  void release() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      ++free_;
+    }
+    cv_.notify_one();
+  }
+
+ private:
+  std::mutex mu_;
+  std::condition_variable cv_;
+  int free_;
+};
+
+// Rendezvous of the block SVDs (Eq. 1) of a batch of instances: every
+// instance deposits its A11 block problems; the last one to arrive runs ONE
+// persistent batched Jacobi launch over the blocks of all instances (the
+// kernel picks its register tile from the largest block and walks the
+// problems of every instance in one cooperative grid), then every instance
+// reads its singular values / orders from its slice of the combined output.
+template <typename T>
+struct BlockRendezvous {
+  std::mutex mu;
+  std::condition_variable cv;
+  int expected = 0, arrived = 0;
+  bool done = false;
+  struct Entry {
+    const std::vector<JacobiProblem<T>>* probs = nullptr;
+    double** sig = nullptr;
+    int32_t** perm = nullptr;
+  };
+  std::vector<Entry> entries;
+  JacobiStats stats;
+  bool failed = false;
+  Error error{FASTPI_OK, ""};
+  DArr<double> sig_all;
+  DArr<int32_t> perm_all;
+
+  explicit BlockRendezvous(int count) : expected(count), entries(count) {}
+
+  // Instance i arrives (probs == nullptr: it failed before its block SVD).
+  JacobiStats arrive(int i, fastpi_ctx* h, const std::vector<JacobiProblem<T>>* probs, double** sig,
+                     int32_t** perm) {
+    // its blocks must be ready before another stream reads them; a failure
+    // here still registers the instance (without problems), so that the
+    // others are not left waiting
+    bool own_fail = false;
+    Error own_err{FASTPI_OK, ""};
+    if (probs) {
+      const cudaError_t e = cudaStreamSynchronize(h->stream);
+      if (e != cudaSuccess) {
+        own_fail = true;
+        own_err = Error{FASTPI_ERR_CUDA, std::string("cudaStreamSynchronize: ") + cudaGetErrorString(e)};
+        probs = nullptr;
+      }
+    }
+    std::unique_lock<std::mutex> lk(mu);
+    entries[i] = Entry{probs, sig, perm};
+    if (++arrived == expected) {
+      run(h);
+      done = true;
+      lk.unlock();
+      cv.notify_all();
+      lk.lock();
+    } else {
+      cv.wait(lk, [&] { return done; });
+    }
+    if (own_fail) throw own_err;
+    if (failed && probs) throw error;
+    return stats;
+  }
+
+  void run(fastpi_ctx* h) {
+    std::vector<JacobiProblem<T>> all;
+    std::vector<int64_t> off(entries.size(), 0);
+    int64_t tot = 0;
+    for (size_t i = 0; i < entries.size(); ++i) {
+      off[i] = tot;
+      if (!entries[i].probs) continue;
+      for (const auto& pr : *entries[i].probs) {
+        all.push_back(pr);
+        tot += pr.q;
+      }
+    }
+    try {
+      sig_all = DArr<double>(std::max<int64_t>(tot, 1), h->stream);
+      perm_all = DArr<int32_t>(std::max<int64_t>(tot, 1), h->stream);
+      stats = jacobi_svd_batched<T>(h, all, sig_all.get(), perm_all.get());
+      CK(cudaStreamSynchronize(h->stream));
+    } catch (const Error& e) {
+      failed = true;
+      error = e;
+      return;
+    }
+    for (size_t i = 0; i < entries.size(); ++i) {
+      if (!entries[i].probs) continue;
+      *entries[i].sig = sig_all.get() + off[i];
+      *entries[i].perm = perm_all.get() + off[i];
+    }
+  }
+};
+
+template <typename T>
+void factor_batched_impl(fastpi_ctx* const* hs, int count, const int64_t* r, double k, fastpi_precision prec,
+                         int64_t chunk_row, int64_t chunk_col, int concurrency, fastpi_status* status,
+                         std::string* msgs) {
+  BlockRendezvous<T> rv(count);
+  Gate pre(concurrency), post(concurrency);
+  std::vector<std::thread> th;
+  th.reserve(count);
+  for (int i = 0; i < count; ++i) {
+    th.emplace_back([&, i] {
+      fastpi_ctx* h = hs[i];
+      bool arrived = false;
+      bool in_pre = true;
+      pre.acquire();
+      try {
+        CK(cudaSetDevice(h->device));
+        BlockSvdFn<T> bs = [&](const std::vector<JacobiProblem<T>>& probs, double*& sig, int32_t*& perm) {
+          pre.release();
+          in_pre = false;
+          arrived = true;
+          JacobiStats js = rv.arrive(i, h, &probs, &sig, &perm);
+          post.acquire();
+          return js;
+        };
+        factor_into<T>(h, r[i], k, prec, chunk_row, chunk_col, bs);
+        status[i] = FASTPI_OK;
+      } catch (const Error& e) {
+        status[i] = e.status;
+        msgs[i] = e.msg;
+      } catch (const std::exception& e) {
+        status[i] = FASTPI_ERR_CUDA;
+        msgs[i] = e.what();
+      }
+      if (in_pre) pre.release();
+      if (!arrived) {
+        try {
+          rv.arrive(i, h, nullptr, nullptr, nullptr);
+        } catch (...) {
+        }
+      } else {
+        post.release();
+      }
+    });
+  }
+  for (auto& t : th) t.join();
+}
+
+}  // namespace
+
+void factor(fastpi_ctx* h, int64_t r, double k, fastpi_precision prec, int64_t chunk_row, int64_t chunk_col) {
+  if (prec == FASTPI_FP64)
+    factor_into<double>(h, r, k, prec, chunk_row, chunk_col, own_block_svd<double>(h));
+  else
+    factor_into<float>(h, r, k, prec, chunk_row, chunk_col, own_block_svd<float>(h));
+}
+
+void factor_batched(fastpi_ctx* const* hs, int count, const int64_t* r, double k, fastpi_precision prec,
+                    int64_t chunk_row, int64_t chunk_col, int concurrency, fastpi_status* status,
+                    std::string* msgs) {
+  if (prec == FASTPI_FP64)
+    factor_batched_impl<double>(hs, count, r, k, prec, chunk_row, chunk_col, concurrency, status, msgs);
+  else
+    factor_batched_impl<float>(hs, count, r, k, prec, chunk_row, chunk_col, concurrency, status, msgs);
 }
 
 void reorder_only(fastpi_ctx* h, double k) {

@@ -1,6 +1,8 @@
 // Factorization state kept in a handle after fastpi_factor.
 #pragma once
 
+#include <string>
+
 #include "internal.cuh"
 
 namespace fastpi {
@@ -18,6 +20,13 @@ struct Factors {
 };
 
 void factor(fastpi_ctx* h, int64_t r, double k, fastpi_precision prec, int64_t chunk_row, int64_t chunk_col);
+// Independent factorizations of count handles (same device, same precision,
+// one stream each): one host thread per handle, at most `concurrency` of them
+// in the stages before / after the block SVDs at a time, and the A11 block
+// SVDs of all handles in one batched launch.  status[i] / msgs[i] per handle.
+void factor_batched(fastpi_ctx* const* hs, int count, const int64_t* r, double k, fastpi_precision prec,
+                    int64_t chunk_row, int64_t chunk_col, int concurrency, fastpi_status* status,
+                    std::string* msgs);
 // Algorithm 2 alone: the reordering is kept for the permutation / block getters.
 void reorder_only(fastpi_ctx* h, double k);
 void apply_dense(fastpi_ctx* h, const double* Y, int64_t L, int64_t ldy, double* Z, int64_t ldz);

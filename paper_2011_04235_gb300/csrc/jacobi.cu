@@ -487,7 +487,7 @@ JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>
   int nq_max = 1;
   while (nq_max < maxq) nq_max <<= 1;
   size_t smem = size_t(nq_max) * (sizeof(double) + sizeof(int));
-  if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_finish<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  if (smem > 48 * 1024) allow_max_dynamic_smem((const void*)k_finish<T>);
   k_finish<T><<<nprob, 512, smem, st>>>(d_probs, d_sig_off, sig, perm, nq_max);
   CK_LAUNCH();
 
@@ -536,7 +536,7 @@ void jacobi_sort_columns(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& pro
   int nq_max = 1;
   while (nq_max < maxq) nq_max <<= 1;
   size_t smem = size_t(nq_max) * (sizeof(double) + sizeof(int));
-  if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_finish<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  if (smem > 48 * 1024) allow_max_dynamic_smem((const void*)k_finish<T>);
   k_finish<T><<<nprob, 512, smem, st>>>(d_probs, d_sig_off, sig, perm, nq_max);
   CK_LAUNCH();
 }

@@ -596,7 +596,7 @@ bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats,
   int max_smem = 0;
   CK(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, hc->device));
   if (smem > size_t(max_smem)) return false;
-  CK(cudaFuncSetAttribute(k_jacobi_block<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  allow_max_dynamic_smem((const void*)k_jacobi_block<P>);
   int occ = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi_block<P>, BT, smem));
   const int grid = nb / 2;

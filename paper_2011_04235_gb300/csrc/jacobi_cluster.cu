@@ -302,7 +302,7 @@ bool jacobi_svd_cluster(fastpi_ctx* hc, float* K, float* V, int n, double* sig, 
     bytes = blk + tail;
   }
   if (bytes > size_t(max_smem)) return false;
-  CK(cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
+  allow_max_dynamic_smem((const void*)k_jacobi_cluster);
   CK(cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CL);
@@ -353,7 +353,7 @@ bool jacobi_svd_cluster(fastpi_ctx* hc, float* K, float* V, int n, double* sig, 
   CK_LAUNCH();
   if (!with_v) {
     const size_t rs = size_t(REPLAY_ROWS) * qe * sizeof(float) + size_t(REPLAY_BATCH) * np * sizeof(float2);
-    if (rs > 48 * 1024) CK(cudaFuncSetAttribute(k_replay, cudaFuncAttributeMaxDynamicSharedMemorySize, int(rs)));
+    if (rs > 48 * 1024) allow_max_dynamic_smem((const void*)k_replay);
     k_replay<<<(n + REPLAY_ROWS - 1) / REPLAY_ROWS, 256, rs, st>>>(rotlog.get(), out.get(), n, qe, np, R, V);
     CK_LAUNCH();
   }

@@ -45,6 +45,16 @@ void reset_counters() {
   g_jacobi_ms = g_jacobi_flops = 0;
 }
 
+void allow_max_dynamic_smem(const void* func) {
+  int dev = 0, mx = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa;
+  CK(cudaFuncGetAttributes(&fa, func));
+  // the opt-in limit covers static and dynamic shared memory together
+  CK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - int(fa.sharedSizeBytes)));
+}
+
 void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
   if (e == cudaSuccess) return;
   fastpi_status s = (e == cudaErrorMemoryAllocation) ? FASTPI_ERR_OOM : FASTPI_ERR_CUDA;

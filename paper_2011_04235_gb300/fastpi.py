@@ -25,7 +25,7 @@ STATUS = {0: "FASTPI_OK", 1: "FASTPI_ERR_ARG", 2: "FASTPI_ERR_CSR", 3: "FASTPI_E
           5: "FASTPI_ERR_NO_CONVERGENCE", 6: "FASTPI_ERR_STATE"}
 
 # every symbol the header declares
-SYMBOLS = ["fastpi_create", "fastpi_factor", "fastpi_reorder", "fastpi_apply", "fastpi_apply_host", "fastpi_apply_csr",
+SYMBOLS = ["fastpi_create", "fastpi_factor", "fastpi_factor_batched", "fastpi_reorder", "fastpi_apply", "fastpi_apply_host", "fastpi_apply_csr",
            "fastpi_residual", "fastpi_residual_noalloc", "fastpi_get_rank", "fastpi_get_S", "fastpi_get_U",
            "fastpi_get_V",
            "fastpi_get_perm", "fastpi_get_blocks", "fastpi_get_info", "fastpi_get_counters",
@@ -81,6 +81,23 @@ def residual_noalloc(m: int, n: int, rowptr: torch.Tensor, col: torch.Tensor, va
 ENGINES = {"simt": 0, "tf32": 1, "tf32x3": 3}
 
 
+def factor_batched(handles, ranks, k: float, precision="mixed", chunk_row: int = 0, chunk_col: int = 0,
+                   concurrency: int = 0):
+    """fastpi_factor_batched over FastPI objects (each created on its own stream
+    for concurrency).  Returns the per-handle status list; raises on the first
+    failure."""
+    count = len(handles)
+    hs = (C.c_void_p * count)(*[h._h for h in handles])
+    rs = (C.c_int64 * count)(*[int(r) for r in ranks])
+    st = (C.c_int * count)()
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    with torch.cuda.device(handles[0].device):
+        _check(lib().fastpi_factor_batched(C.cast(hs, C.c_void_p), count, C.cast(rs, C.c_void_p), float(k), prec,
+                                           int(chunk_row), int(chunk_col), int(concurrency),
+                                           C.cast(st, C.c_void_p)))
+    return list(st)
+
+
 def gemm_f32(A: torch.Tensor, B: torch.Tensor, ta: bool = False, tb: bool = False, engine: str = "tf32x3",
              alpha: float = 1.0, beta: float = 0.0, Cout: torch.Tensor | None = None) -> torch.Tensor:
     """C = alpha op(A) op(B) + beta C through fastpi_gemm_f32 (device float32
@@ -108,6 +125,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fastpi_create": ([C.POINTER(p), i64, i64, i64, vp, vp, vp, i32, vp], i32),
         "fastpi_factor": ([p, i64, dbl, i32, i64, i64], i32),
         "fastpi_reorder": ([p, dbl], i32),
+        "fastpi_factor_batched": ([vp, i32, vp, dbl, i32, i64, i64, i32, vp], i32),
         "fastpi_apply": ([p, vp, i64, i64, vp, i64], i32),
         "fastpi_apply_host": ([p, vp, i64, i64, vp, i64], i32),
         "fastpi_apply_csr": ([p, i64, i64, vp, vp, vp, vp, i64], i32),
