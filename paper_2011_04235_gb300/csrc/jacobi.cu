@@ -136,12 +136,15 @@ __global__ void k_fro2(const DevProb<T>* probs, double* fro2) {
 }
 
 template <typename T>
-__global__ void k_init_v(const DevProb<T>* probs) {
-  const DevProb<T> pr = probs[blockIdx.y];
-  int64_t n = int64_t(pr.q) * pr.q;
-  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x) {
-    int64_t c = t / pr.q, r = t % pr.q;
-    pr.V[c * pr.ldv + r] = (r == c) ? T(1) : T(0);
+__global__ void k_init_v(const DevProb<T>* probs, int nprob) {
+  // problems strided over grid.y (a batch may hold more than 65 535 problems)
+  for (int b = blockIdx.y; b < nprob; b += gridDim.y) {
+    const DevProb<T> pr = probs[b];
+    const int64_t n = int64_t(pr.q) * pr.q;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x) {
+      const int64_t c = t / pr.q, r = t % pr.q;
+      pr.V[c * pr.ldv + r] = (r == c) ? T(1) : T(0);
+    }
   }
 }
 
@@ -420,8 +423,8 @@ JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>
   }
   CK(cudaMemcpyAsync(d_probs.get(), dp.data(), sizeof(DevProb<T>) * nprob, cudaMemcpyHostToDevice, st));
   {
-    dim3 g(unsigned(std::min<int64_t>(64, (int64_t(maxq) * maxq + 255) / 256)), unsigned(nprob));
-    k_init_v<T><<<g, 256, 0, st>>>(d_probs);
+    dim3 g(unsigned(std::min<int64_t>(64, (int64_t(maxq) * maxq + 255) / 256)), unsigned(std::min(nprob, 65535)));
+    k_init_v<T><<<g, 256, 0, st>>>(d_probs, nprob);
     CK_LAUNCH();
   }
   DArr<ProbState> state(nprob, st);

@@ -2,6 +2,12 @@
 factorization statistics (the same call sequence as one bench step).
 
   python -m paper_2011_04235_gb300.run_workload medium mixed [chunk_row] [chunk_col]
+
+The many-instance workload (independent matrices, m log-uniform in
+[1 000, 50 000], n = m / 4, nnz = 10 m, r = n / 10, Y m x 200) is timed one
+instance after another and through fastpi_factor_batched:
+
+  python -m paper_2011_04235_gb300.run_workload many [count] [precision] [concurrency[,concurrency...]]
 """
 from __future__ import annotations
 
@@ -19,7 +25,56 @@ import workloads  # noqa: E402
 from paper_2011_04235_gb300 import fastpi  # noqa: E402
 
 
+def run_many(count: int, prec: str, concurrency: list):
+    import time
+    ws = workloads.make_many(count)
+    dev = "cuda:0"
+    streams = [torch.cuda.Stream(device=dev) for _ in ws]
+    csr = [tuple(torch.from_numpy(a).to(dev) for a in (w["rowptr"], w["col"], w["val"])) for w in ws]
+    Ys = [torch.from_numpy(w["Y"]).to(dev) for w in ws]
+    torch.cuda.synchronize()
+    res = {"instances": count, "rows": int(sum(w["m"] for w in ws)), "nnz": int(sum(w["col"].size for w in ws)),
+           "precision": prec, "k": 0.01, "chunk": 256}
+
+    # one after another, one stream
+    hs = [fastpi.FastPI(w["m"], w["n"], *c, device=dev) for w, c in zip(ws, csr)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for w, h, Y in zip(ws, hs, Ys):
+        h.factor(w["r"], 0.01, prec, 256, 256)
+        h.apply(Y)
+    torch.cuda.synchronize()
+    res["sequential_s"] = time.perf_counter() - t0
+    seq_res = [None] * count
+    for i, (h, Y) in enumerate(zip(hs, Ys)):
+        seq_res[i] = h.residual(Y, h.apply(Y))
+        h.close()
+
+    # batched: one stream per instance, for each requested concurrency
+    for conc in concurrency:
+        hs = [fastpi.FastPI(w["m"], w["n"], *c, device=dev, stream=s.cuda_stream)
+              for w, c, s in zip(ws, csr, streams)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fastpi.factor_batched(hs, [w["r"] for w in ws], 0.01, prec, 256, 256, concurrency=conc)
+        Zs = [h.apply(Y) for h, Y in zip(hs, Ys)]
+        torch.cuda.synchronize()
+        bt = time.perf_counter() - t0
+        gap = 0.0
+        for h, Y, Z, r0 in zip(hs, Ys, Zs, seq_res):
+            gap = max(gap, abs(h.residual(Y, Z) - r0) / max(r0, 1e-300))
+            h.close()
+        res[f"batched_s_concurrency_{conc}"] = bt
+        res[f"speedup_concurrency_{conc}"] = res["sequential_s"] / bt
+        res[f"max_rel_residual_diff_concurrency_{conc}"] = gap
+    print(json.dumps(res))
+
+
 def main(argv):
+    if len(argv) > 1 and argv[1] == "many":
+        run_many(int(argv[2]) if len(argv) > 2 else 256, argv[3] if len(argv) > 3 else "mixed",
+                 [int(c) for c in (argv[4] if len(argv) > 4 else "8").split(",")])
+        return
     name = argv[1] if len(argv) > 1 else "medium"
     prec = argv[2] if len(argv) > 2 else "mixed"
     cr = int(argv[3]) if len(argv) > 3 else 256
