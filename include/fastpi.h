@@ -174,6 +174,28 @@ fastpi_status fastpi_factor_batched(fastpi_t* hs, int count, const int64_t* r, d
                                     int64_t chunk_row, int64_t chunk_col, int concurrency,
                                     fastpi_status* status_out);
 
+/* Factor reuse (serving the apply of Application 1 from stored factors):
+ * a handle that holds the given rank-r factors of an m x n matrix -- S (host,
+ * r values, descending, >= 0), U (m x r) and V (n x r), row-major FP64 with
+ * leading dimensions ldu, ldv >= r, in the caller's original row / column
+ * order (as fastpi_get_U / _V return them), on the device when
+ * ptrs_on_device != 0, else on the host.  The inputs are copied; the mixed
+ * precision stores U and V in FP32 as fastpi_factor would.  The handle
+ * serves fastpi_apply, fastpi_apply_host, fastpi_apply_csr and the factor
+ * getters; it has no matrix, so fastpi_factor, fastpi_reorder and
+ * fastpi_residual return FASTPI_ERR_STATE.  Errors: FASTPI_ERR_ARG (sizes,
+ * null arrays, unsorted or negative S), FASTPI_ERR_OOM, FASTPI_ERR_CUDA. */
+fastpi_status fastpi_create_from_factors(fastpi_t* out, int64_t m, int64_t n, int64_t r, const double* S,
+                                        const double* U, int64_t ldu, const double* V, int64_t ldv,
+                                        fastpi_precision prec, int ptrs_on_device, void* cuda_stream);
+
+/* Keep the r largest triplets of the current factors (a sweep over smaller
+ * target ranks -- alpha = r / n -- from one factorization; an approximation
+ * of fastpi_factor at rank r, whose appends truncate at r along the way).
+ * r >= the current rank leaves the factors unchanged.  Errors:
+ * FASTPI_ERR_ARG (r < 1), FASTPI_ERR_STATE (no factors). */
+fastpi_status fastpi_truncate(fastpi_t h, int64_t r);
+
 /* Algorithm 2 (Section 3.2) alone: the hub-and-spoke reordering of A for hub
  * ratio k in (0, 1), without any factorization.  Afterwards fastpi_get_perm,
  * fastpi_get_blocks and fastpi_get_info (reordering fields; the factorization

@@ -1,5 +1,6 @@
 // C ABI of libfastpi (declared in include/fastpi.h).  Every entry point
 // converts internal errors into a status code and a message.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -112,6 +113,7 @@ fastpi_status fastpi_factor(fastpi_t h, int64_t r, double k, fastpi_precision pr
   require(k > 0.0 && k < 1.0 && std::isfinite(k), FASTPI_ERR_ARG, "hub ratio k must lie in (0, 1)");
   require(prec == FASTPI_FP64 || prec == FASTPI_MIXED_TF32, FASTPI_ERR_ARG, "unknown precision");
   require(chunk_row >= 0 && chunk_col >= 0, FASTPI_ERR_ARG, "chunk sizes must be >= 0");
+  require(h->has_matrix, FASTPI_ERR_STATE, "handle made from factors has no matrix");
   h->factored = false;
   h->reordered = false;
   fastpi::factor(h, r, k, prec, chunk_row, chunk_col);
@@ -130,6 +132,7 @@ fastpi_status fastpi_factor_batched(fastpi_t* hs, int count, const int64_t* r, d
       require(hs[i] != nullptr, FASTPI_ERR_ARG, "null handle in the batch");
       require(r[i] >= 1, FASTPI_ERR_ARG, "every target rank must be >= 1");
       require(hs[i]->device == hs[0]->device, FASTPI_ERR_ARG, "all handles of a batch must be on one device");
+      require(hs[i]->has_matrix, FASTPI_ERR_ARG, "a handle made from factors has no matrix");
       for (int j = 0; j < i; ++j) require(hs[j] != hs[i], FASTPI_ERR_ARG, "a handle appears twice in the batch");
     }
   } catch (const Error& e) {
@@ -160,11 +163,60 @@ fastpi_status fastpi_factor_batched(fastpi_t* hs, int count, const int64_t* r, d
   return first;
 }
 
+fastpi_status fastpi_create_from_factors(fastpi_t* out, int64_t m, int64_t n, int64_t r, const double* S,
+                                        const double* U, int64_t ldu, const double* V, int64_t ldv,
+                                        fastpi_precision prec, int ptrs_on_device, void* cuda_stream) {
+  if (out) *out = nullptr;
+  fastpi_ctx* h = nullptr;
+  try {
+    require(out != nullptr, FASTPI_ERR_ARG, "out is NULL");
+    require(m >= 1 && n >= 1 && r >= 0 && r <= std::min(m, n), FASTPI_ERR_ARG, "need m, n >= 1, 0 <= r <= min(m, n)");
+    require(prec == FASTPI_FP64 || prec == FASTPI_MIXED_TF32, FASTPI_ERR_ARG, "unknown precision");
+    require(r == 0 || (S && U && V), FASTPI_ERR_ARG, "null factor array");
+    require(ldu >= r && ldv >= r, FASTPI_ERR_ARG, "leading dimension smaller than r");
+    for (int64_t i = 0; i < r; ++i) {
+      require(std::isfinite(S[i]) && S[i] >= 0.0, FASTPI_ERR_ARG, "singular values must be finite and >= 0");
+      require(i == 0 || S[i] <= S[i - 1], FASTPI_ERR_ARG, "singular values must be in descending order");
+    }
+    h = new fastpi_ctx();
+    CK(cudaGetDevice(&h->device));
+    CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->m = m;
+    h->n = n;
+    h->nnz = 0;
+    h->has_matrix = false;
+    h->dstatus = DArr<unsigned>(1, h->stream);
+    fastpi::load_factors(h, r, S, U, ldu, V, ldv, prec, ptrs_on_device != 0);
+    *out = h;
+    return FASTPI_OK;
+  } catch (const Error& e) {
+    g_create_error = e.msg;
+    delete h;
+    return e.status;
+  } catch (const std::exception& e) {
+    g_create_error = e.what();
+    delete h;
+    return FASTPI_ERR_CUDA;
+  }
+}
+
+fastpi_status fastpi_truncate(fastpi_t h, int64_t r) {
+  if (!h) return FASTPI_ERR_ARG;
+  API_BEGIN
+  use_device(h);
+  require_factored(h);
+  require(r >= 1, FASTPI_ERR_ARG, "rank must be >= 1");
+  fastpi::truncate_factors(h, r);
+  API_END(h)
+}
+
 fastpi_status fastpi_reorder(fastpi_t h, double k) {
   if (!h) return FASTPI_ERR_ARG;
   API_BEGIN
   use_device(h);
   require(k > 0.0 && k < 1.0 && std::isfinite(k), FASTPI_ERR_ARG, "hub ratio k must lie in (0, 1)");
+  require(h->has_matrix, FASTPI_ERR_STATE, "handle made from factors has no matrix");
   h->factored = false;
   h->reordered = false;
   fastpi::reorder_only(h, k);
@@ -220,6 +272,7 @@ fastpi_status fastpi_residual(fastpi_t h, const double* Y, int64_t L, int64_t ld
   use_device(h);
   require(out != nullptr, FASTPI_ERR_ARG, "out is NULL");
   require(L >= 0 && ldy >= L && ldz >= L, FASTPI_ERR_ARG, "need L >= 0, ldy >= L, ldz >= L");
+  require(h->has_matrix, FASTPI_ERR_STATE, "handle made from factors has no matrix");
   *out = residual(h, Y, L, ldy, Z, ldz);
   API_END(h)
 }
@@ -303,7 +356,7 @@ fastpi_status fastpi_get_blocks(fastpi_t h, int64_t* B, int64_t* row_off, int64_
 fastpi_status fastpi_get_info(fastpi_t h, fastpi_info* info) {
   if (!h) return FASTPI_ERR_ARG;
   API_BEGIN
-  require_reordered(h);
+  require((h->reordered || h->factored) && h->fac, FASTPI_ERR_STATE, "call fastpi_reorder or fastpi_factor first");
   require(info != nullptr, FASTPI_ERR_ARG, "info is NULL");
   *info = h->info;
   API_END(h)

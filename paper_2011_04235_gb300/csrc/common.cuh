@@ -83,6 +83,7 @@ struct fastpi_ctx {
   // results
   bool factored = false;
   bool reordered = false;   // fac->R holds Algorithm 2's result (after fastpi_reorder or fastpi_factor)
+  bool has_matrix = true;   // false for a handle made from given factors (apply only)
   fastpi::Factors* fac = nullptr;
   fastpi_info info{};
   std::string last_error;

@@ -1391,6 +1391,86 @@ void factor_batched(fastpi_ctx* const* hs, int count, const int64_t* r, double k
     factor_batched_impl<float>(hs, count, r, k, prec, chunk_row, chunk_col, concurrency, status, msgs);
 }
 
+void load_factors(fastpi_ctx* h, int64_t r, const double* S, const double* U, int64_t ldu, const double* V,
+                  int64_t ldv, fastpi_precision prec, bool on_device) {
+  cudaStream_t st = h->stream;
+  Factors* F = new Factors();
+  try {
+    F->prec = int(prec);
+    F->m = h->m;
+    F->n = h->n;
+    F->rank = r;
+    F->S.assign(S, S + r);
+    const int64_t ldr = std::max<int64_t>(r, 1);
+    F->S_d = DArr<double>(ldr, st);
+    if (r > 0) CK(cudaMemcpyAsync(F->S_d.get(), S, size_t(r) * 8, cudaMemcpyHostToDevice, st));
+    // stage host inputs on the device, then copy / convert into the packed layout
+    DArr<double> Ud, Vd;
+    const double* Us = U;
+    const double* Vs = V;
+    int64_t lu = ldu, lv = ldv;
+    if (!on_device && r > 0) {
+      Ud = DArr<double>(h->m * r, st);
+      Vd = DArr<double>(h->n * r, st);
+      CK(cudaMemcpy2DAsync(Ud.get(), size_t(r) * 8, U, size_t(ldu) * 8, size_t(r) * 8, size_t(h->m),
+                           cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpy2DAsync(Vd.get(), size_t(r) * 8, V, size_t(ldv) * 8, size_t(r) * 8, size_t(h->n),
+                           cudaMemcpyHostToDevice, st));
+      Us = Ud.get();
+      Vs = Vd.get();
+      lu = lv = r;
+    }
+    if (prec == FASTPI_FP64) {
+      F->U64 = DArr<double>(h->m * ldr, st);
+      F->V64 = DArr<double>(h->n * ldr, st);
+      copy2d<double, double>(st, h->m, r, Us, lu, F->U64.get(), ldr);
+      copy2d<double, double>(st, h->n, r, Vs, lv, F->V64.get(), ldr);
+    } else {
+      F->U32 = DArr<float>(h->m * ldr, st);
+      F->V32 = DArr<float>(h->n * ldr, st);
+      copy2d<float, double>(st, h->m, r, Us, lu, F->U32.get(), ldr);
+      copy2d<float, double>(st, h->n, r, Vs, lv, F->V32.get(), ldr);
+    }
+    CK(cudaStreamSynchronize(st));
+  } catch (...) {
+    delete F;
+    throw;
+  }
+  delete h->fac;
+  h->fac = F;
+  h->factored = true;
+  h->reordered = false;
+  h->info = fastpi_info{};
+  h->info.m = h->m;
+  h->info.n = h->n;
+  h->info.rank = r;
+  h->info.precision = int(prec);
+}
+
+void truncate_factors(fastpi_ctx* h, int64_t r) {
+  Factors& F = *h->fac;
+  if (r >= F.rank) return;
+  cudaStream_t st = h->stream;
+  const int64_t ldo = std::max<int64_t>(F.rank, 1), ldr = std::max<int64_t>(r, 1);
+  if (F.prec == FASTPI_FP64) {
+    DArr<double> U(F.m * ldr, st), V(F.n * ldr, st);
+    copy2d<double, double>(st, F.m, r, F.U64.get(), ldo, U.get(), ldr);
+    copy2d<double, double>(st, F.n, r, F.V64.get(), ldo, V.get(), ldr);
+    F.U64 = std::move(U);
+    F.V64 = std::move(V);
+  } else {
+    DArr<float> U(F.m * ldr, st), V(F.n * ldr, st);
+    copy2d<float, float>(st, F.m, r, F.U32.get(), ldo, U.get(), ldr);
+    copy2d<float, float>(st, F.n, r, F.V32.get(), ldo, V.get(), ldr);
+    F.U32 = std::move(U);
+    F.V32 = std::move(V);
+  }
+  F.S.resize(r);
+  F.rank = r;
+  h->info.rank = r;
+  CK(cudaStreamSynchronize(st));
+}
+
 void reorder_only(fastpi_ctx* h, double k) {
   Factors* F = new Factors();
   h->info = fastpi_info{};

@@ -27,6 +27,13 @@ void factor(fastpi_ctx* h, int64_t r, double k, fastpi_precision prec, int64_t c
 void factor_batched(fastpi_ctx* const* hs, int count, const int64_t* r, double k, fastpi_precision prec,
                     int64_t chunk_row, int64_t chunk_col, int concurrency, fastpi_status* status,
                     std::string* msgs);
+// Factors given by the caller (U m x r, V n x r row-major FP64, host or device;
+// S host, r values): the handle serves fastpi_apply* as if fastpi_factor had
+// produced them (the mixed form stores U, V in FP32).
+void load_factors(fastpi_ctx* h, int64_t r, const double* S, const double* U, int64_t ldu, const double* V,
+                  int64_t ldv, fastpi_precision prec, bool on_device);
+// Keep the r largest triplets of the current factors.
+void truncate_factors(fastpi_ctx* h, int64_t r);
 // Algorithm 2 alone: the reordering is kept for the permutation / block getters.
 void reorder_only(fastpi_ctx* h, double k);
 void apply_dense(fastpi_ctx* h, const double* Y, int64_t L, int64_t ldy, double* Z, int64_t ldz);

@@ -25,7 +25,8 @@ STATUS = {0: "FASTPI_OK", 1: "FASTPI_ERR_ARG", 2: "FASTPI_ERR_CSR", 3: "FASTPI_E
           5: "FASTPI_ERR_NO_CONVERGENCE", 6: "FASTPI_ERR_STATE"}
 
 # every symbol the header declares
-SYMBOLS = ["fastpi_create", "fastpi_factor", "fastpi_factor_batched", "fastpi_reorder", "fastpi_apply", "fastpi_apply_host", "fastpi_apply_csr",
+SYMBOLS = ["fastpi_create", "fastpi_create_from_factors", "fastpi_truncate", "fastpi_factor",
+           "fastpi_factor_batched", "fastpi_reorder", "fastpi_apply", "fastpi_apply_host", "fastpi_apply_csr",
            "fastpi_residual", "fastpi_residual_noalloc", "fastpi_get_rank", "fastpi_get_S", "fastpi_get_U",
            "fastpi_get_V",
            "fastpi_get_perm", "fastpi_get_blocks", "fastpi_get_info", "fastpi_get_counters",
@@ -125,6 +126,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fastpi_create": ([C.POINTER(p), i64, i64, i64, vp, vp, vp, i32, vp], i32),
         "fastpi_factor": ([p, i64, dbl, i32, i64, i64], i32),
         "fastpi_reorder": ([p, dbl], i32),
+        "fastpi_create_from_factors": ([C.POINTER(p), i64, i64, i64, vp, vp, i64, vp, i64, i32, i32, vp], i32),
+        "fastpi_truncate": ([p, i64], i32),
         "fastpi_factor_batched": ([vp, i32, vp, dbl, i32, i64, i64, i32, vp], i32),
         "fastpi_apply": ([p, vp, i64, i64, vp, i64], i32),
         "fastpi_apply_host": ([p, vp, i64, i64, vp, i64], i32),
@@ -219,6 +222,46 @@ class FastPI:
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         with torch.cuda.device(self.device):
             _check(lib().fastpi_factor(self._h, int(r), float(k), prec, int(chunk_row), int(chunk_col)), self._h)
+        return self
+
+    @classmethod
+    def from_factors(cls, S, U: torch.Tensor, V: torch.Tensor, precision="fp64", device="cuda:0", stream=None):
+        """A handle that serves applies from given factors (S host array, U and V
+        FP64 device tensors, m x r and n x r, original row / column order)."""
+        self = cls.__new__(cls)
+        self.device = torch.device(device)
+        self.m, self.n = int(U.shape[0]), int(V.shape[0])
+        self.nnz = 0
+        r = int(U.shape[1])
+        S = np.ascontiguousarray(S, dtype=np.float64)
+        U = U.to(self.device, torch.float64)
+        V = V.to(self.device, torch.float64)
+        U = U if U.stride(1) == 1 else U.contiguous()
+        V = V if V.stride(1) == 1 else V.contiguous()
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self._h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            st = stream if stream is not None else _stream_ptr(self.device)
+            self._stream = st
+            _check(lib().fastpi_create_from_factors(C.byref(self._h), self.m, self.n, r, S.ctypes.data, _ptr(U),
+                                                    max(U.stride(0), 1), _ptr(V), max(V.stride(0), 1), prec, 1,
+                                                    st))
+        return self
+
+    def save(self, path: str):
+        """Store (S, U, V) and the precision as a .npz file (factor reuse)."""
+        inf = self.info()
+        np.savez(path, S=self.S(), U=self.U().cpu().numpy(), V=self.V().cpu().numpy(),
+                 precision=np.int64(inf["precision"]))
+
+    @classmethod
+    def load(cls, path: str, device="cuda:0", stream=None):
+        d = np.load(path)
+        return cls.from_factors(d["S"], torch.from_numpy(d["U"]), torch.from_numpy(d["V"]),
+                                precision=int(d["precision"]), device=device, stream=stream)
+
+    def truncate(self, r: int):
+        _check(lib().fastpi_truncate(self._h, int(r)), self._h)
         return self
 
     def reorder(self, k: float):
