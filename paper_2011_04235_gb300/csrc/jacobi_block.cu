@@ -172,16 +172,43 @@ __device__ __forceinline__ void cp_async_wait() {
 // threads 0..P/2-1 compute the rotations of the round's pairs, then all
 // threads update the P x P entries of G <- J^T G J and Q <- Q J.  Returns
 // the buffer that holds the final Q.  Runs `sweeps` sweeps.
+// Pairs of one inner round.  Full rounds (cross = false): the circle method
+// over all P columns, P - 1 rounds.  Cross rounds (cross = true): column i of
+// the first block with column B + (i + ir) mod B of the second, B rounds.
+template <int P>
+__device__ __forceinline__ void inner_pair(bool cross, int k, int ir, int& p, int& q) {
+  constexpr int B = P / 2;
+  if (cross) {
+    p = k;
+    q = B + (k + ir) % B;
+  } else {
+    circle_pair(k, ir, P, p, q);
+  }
+}
+template <int P>
+__device__ __forceinline__ int inner_mate(bool cross, int i, int ir) {
+  constexpr int B = P / 2;
+  if (!cross) return circle_mate(i, ir, P);
+  return i < B ? B + (i + ir) % B : ((i - B - ir) % B + B) % B;
+}
+
+// Whole CTA, any P: G and Q in shared memory, double-buffered.  Per round,
+// threads 0..P/2-1 compute the rotations of the round's pairs, then all
+// threads update the P x P entries of G <- J^T G J and Q <- Q J.  Returns
+// the buffer that holds the final Q.  `cross`: only the pairs across the two
+// blocks (the pairs inside each block were visited in the first round of
+// the sweep).
 template <int P>
 __device__ __forceinline__ float* inner_solve_cta(float* G, float* Gn, float* Q, float* Qn, float* sc, float* so,
                                                   int tid, float tabs, float tol2, float early2, int sweeps,
-                                                  int* s_rot, int* s_pair_rot) {
+                                                  bool cross, int* s_rot, int* s_pair_rot) {
   constexpr int GS = P + 1;
+  const int rounds = cross ? P / 2 : P - 1;
   for (int is = 0; is < sweeps; ++is) {
-    for (int ir = 0; ir < P - 1; ++ir) {
+    for (int ir = 0; ir < rounds; ++ir) {
       if (tid < P / 2) {
         int p, q;
-        circle_pair(tid, ir, P, p, q);
+        inner_pair<P>(cross, tid, ir, p, q);
         const float al = G[p * GS + p], be = G[q * GS + q], ga = G[p * GS + q];
         float c = 1.f, s = 0.f;
         if (al > tabs && be > tabs && ga * ga > tol2 * al * be) {
@@ -205,7 +232,7 @@ __device__ __forceinline__ float* inner_solve_cta(float* G, float* Gn, float* Q,
       __syncthreads();
       for (int e = tid; e < P * P; e += BT) {
         const int i = e / P, j = e % P;
-        const int mi = circle_mate(i, ir, P), mj = circle_mate(j, ir, P);
+        const int mi = inner_mate<P>(cross, i, ir), mj = inner_mate<P>(cross, j, ir);
         const float ci = sc[i], si = so[i], cj = sc[j], sj = so[j];
         Gn[i * GS + j] = ci * (cj * G[i * GS + j] + sj * G[i * GS + mj]) +
                          si * (cj * G[mi * GS + j] + sj * G[mi * GS + mj]);
@@ -468,7 +495,11 @@ __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
           }
         }
       } else {
-        Qf = inner_solve_cta<P>(G, Gn, Q, Qn, s_sc, s_so, tid, tabs, tol2, early2, a.inner, &s_rot, &s_pair_rot);
+        // the pairs inside the blocks in the first round of a sweep (every
+        // block meets its first partner there), only cross pairs afterwards:
+        // every column pair is still visited at least once per sweep
+        Qf = inner_solve_cta<P>(G, Gn, Q, Qn, s_sc, s_so, tid, tabs, tol2, early2, a.inner, rr != 0, &s_rot,
+                                &s_pair_rot);
       }
       PHASE_MARK(2);
       cp_async_wait<0>();
