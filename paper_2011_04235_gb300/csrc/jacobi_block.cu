@@ -202,7 +202,7 @@ template <int P>
 __device__ __forceinline__ float* inner_solve_cta(float* G, float* Gn, float* Q, float* Qn, float* sc, float* so,
                                                   int tid, float tabs, float tol2, float early2, int sweeps,
                                                   bool cross, int* s_rot, int* s_pair_rot) {
-  constexpr int GS = P + 1;
+  constexpr int GS = P;
   const int rounds = cross ? P / 2 : P - 1;
   for (int is = 0; is < sweeps; ++is) {
     for (int ir = 0; ir < rounds; ++ir) {
@@ -258,7 +258,7 @@ __device__ __forceinline__ float* inner_solve_cta(float* G, float* Gn, float* Q,
 template <int P>
 __device__ __forceinline__ void inner_solve_regs(const float* G, float* Q, int lane, float tabs, float tol2,
                                                  float early2, int sweeps, int& rotmax) {
-  constexpr int GS = P + 1;
+  constexpr int GS = P;
   const bool isg = lane < P, isq = lane >= P && lane < 2 * P;
   const int ri = isg ? lane : (isq ? lane - P : 0);
   float v[P];
@@ -365,7 +365,7 @@ template <int P>
 __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
   constexpr int B = P / 2;         // columns per block
   constexpr int TW = P / 4;        // Gram tile edge (4 x 4 tiles of TW x TW)
-  constexpr int GS = P + 1;        // padded row stride of G and Q
+  constexpr int GS = P;            // row stride of G and Q (a warp covers whole rows: no bank conflicts)
   extern __shared__ float4 smem4[];
   const int ldk = a.ldk, n = a.n;
   float* Xs = reinterpret_cast<float*>(smem4);   // [P][ldk]
@@ -505,28 +505,41 @@ __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
       cp_async_wait<0>();
       __syncthreads();
       PHASE_MARK(6);
-      // 4. K_IJ <- X Q, V_IJ <- Y Q (one row per thread); nothing to write
-      // when no pair of the block pair rotated (Q = I)
-      for (int r = tid; s_pair_rot && r < n; r += BT) {
-        float x[P], y[P];
+      // 4. K_IJ <- X Q, V_IJ <- Y Q; one item = one row and one half of the P
+      // output columns (items of one warp share the half, so every store
+      // instruction writes 32 consecutive rows of one column); nothing to
+      // write when no pair of the block pair rotated (Q = I)
+      {
+        constexpr int H = P / 2;
+        for (int it = tid; s_pair_rot && it < 2 * n; it += BT) {
+          const int half = it >= n ? 1 : 0, r = it - half * n, j0 = half * H;
+          float u[H], v[H];
 #pragma unroll
-        for (int c = 0; c < P; ++c) {
-          x[c] = Xs[size_t(c) * ldk + r];
-          y[c] = Ys[size_t(c) * ldk + r];
-        }
-#pragma unroll 2
-        for (int j = 0; j < P; ++j) {
-          const int g = s_gcol[j];
-          float u = 0.f, v = 0.f;
+          for (int j = 0; j < H; ++j) u[j] = v[j] = 0.f;
 #pragma unroll
           for (int c = 0; c < P; ++c) {
-            const float qc = Qf[c * GS + j];
-            u = fmaf(x[c], qc, u);
-            v = fmaf(y[c], qc, v);
+            const float xc = Xs[size_t(c) * ldk + r], yc = Ys[size_t(c) * ldk + r];
+            const float4* q4 = reinterpret_cast<const float4*>(Qf + c * GS + j0);
+#pragma unroll
+            for (int j4 = 0; j4 < H / 4; ++j4) {
+              const float4 q = q4[j4];
+              u[4 * j4 + 0] = fmaf(xc, q.x, u[4 * j4 + 0]);
+              u[4 * j4 + 1] = fmaf(xc, q.y, u[4 * j4 + 1]);
+              u[4 * j4 + 2] = fmaf(xc, q.z, u[4 * j4 + 2]);
+              u[4 * j4 + 3] = fmaf(xc, q.w, u[4 * j4 + 3]);
+              v[4 * j4 + 0] = fmaf(yc, q.x, v[4 * j4 + 0]);
+              v[4 * j4 + 1] = fmaf(yc, q.y, v[4 * j4 + 1]);
+              v[4 * j4 + 2] = fmaf(yc, q.z, v[4 * j4 + 2]);
+              v[4 * j4 + 3] = fmaf(yc, q.w, v[4 * j4 + 3]);
+            }
           }
-          if (g >= 0) {
-            __stcg(a.K + size_t(g) * ldk + r, u);
-            __stcg(a.V + size_t(g) * ldk + r, v);
+#pragma unroll
+          for (int j = 0; j < H; ++j) {
+            const int g = s_gcol[j0 + j];
+            if (g >= 0) {
+              __stcg(a.K + size_t(g) * ldk + r, u[j]);
+              __stcg(a.V + size_t(g) * ldk + r, v[j]);
+            }
           }
         }
       }
@@ -612,7 +625,7 @@ __global__ void k_b_pad_out(const float* __restrict__ Kp, const float* __restric
 
 template <int P>
 size_t block_smem(int ldk) {
-  return (2 * size_t(P) * ldk + 4 * size_t(P) * (P + 1)) * sizeof(float);
+  return (2 * size_t(P) * ldk + 4 * size_t(P) * P) * sizeof(float);
 }
 
 template <int P>
