@@ -361,7 +361,10 @@ struct BlkArgs {
   unsigned* status;
 };
 
-template <int P>
+// VS: the V panel is staged in shared memory next to the K panel (false: the
+// update reads V's rows straight from L2, for cores whose two panels do not
+// fit in one CTA's shared memory).
+template <int P, bool VS>
 __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
   constexpr int B = P / 2;         // columns per block
   constexpr int TW = P / 4;        // Gram tile edge (4 x 4 tiles of TW x TW)
@@ -369,8 +372,8 @@ __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
   extern __shared__ float4 smem4[];
   const int ldk = a.ldk, n = a.n;
   float* Xs = reinterpret_cast<float*>(smem4);   // [P][ldk]
-  float* Ys = Xs + size_t(P) * ldk;              // [P][ldk]
-  float* G = Ys + size_t(P) * ldk;               // [P][GS]
+  float* Ys = Xs + size_t(P) * ldk;              // [P][ldk] (VS only)
+  float* G = Ys + (VS ? size_t(P) * ldk : 0);    // [P][GS]
   float* Q = G + P * GS;                         // [P][GS]
   float* Gn = Q + P * GS;                        // [P][GS] (second buffers of the Gram solve)
   float* Qn = Gn + P * GS;                       // [P][GS]
@@ -433,14 +436,16 @@ __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
           *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
       }
       cp_async_commit();
-      for (int e = tid; e < P * nq; e += BT) {
-        const int c = e / nq, r4 = (e - c * nq) * 4;
-        const int g = s_gcol[c];
-        float* d = Ys + size_t(c) * ldk + r4;
-        if (g >= 0)
-          cp_async16(d, a.V + size_t(g) * ldk + r4);
-        else
-          *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (VS) {
+        for (int e = tid; e < P * nq; e += BT) {
+          const int c = e / nq, r4 = (e - c * nq) * 4;
+          const int g = s_gcol[c];
+          float* d = Ys + size_t(c) * ldk + r4;
+          if (g >= 0)
+            cp_async16(d, a.V + size_t(g) * ldk + r4);
+          else
+            *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
       }
       cp_async_commit();
       cp_async_wait<1>();
@@ -506,19 +511,30 @@ __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
       __syncthreads();
       PHASE_MARK(6);
       // 4. K_IJ <- X Q, V_IJ <- Y Q; one item = one row and one half of the P
-      // output columns (items of one warp share the half, so every store
-      // instruction writes 32 consecutive rows of one column); nothing to
-      // write when no pair of the block pair rotated (Q = I)
+      // output columns when V is staged (items of one warp share the half, so
+      // every store instruction writes 32 consecutive rows of one column);
+      // nothing to write when no pair of the block pair rotated (Q = I)
       {
-        constexpr int H = P / 2;
-        for (int it = tid; s_pair_rot && it < 2 * n; it += BT) {
+        // with V read from L2 and written in place, one item must own whole
+        // rows (a half-row item would overwrite V entries the other half of
+        // the row still has to read)
+        constexpr int NH = VS ? 2 : 1;
+        constexpr int H = P / NH;
+        for (int it = tid; s_pair_rot && it < NH * n; it += BT) {
           const int half = it >= n ? 1 : 0, r = it - half * n, j0 = half * H;
           float u[H], v[H];
 #pragma unroll
           for (int j = 0; j < H; ++j) u[j] = v[j] = 0.f;
 #pragma unroll
           for (int c = 0; c < P; ++c) {
-            const float xc = Xs[size_t(c) * ldk + r], yc = Ys[size_t(c) * ldk + r];
+            const float xc = Xs[size_t(c) * ldk + r];
+            float yc;
+            if (VS) {
+              yc = Ys[size_t(c) * ldk + r];
+            } else {
+              const int g = s_gcol[c];
+              yc = g >= 0 ? __ldcg(a.V + size_t(g) * ldk + r) : 0.f;
+            }
             const float4* q4 = reinterpret_cast<const float4*>(Qf + c * GS + j0);
 #pragma unroll
             for (int j4 = 0; j4 < H / 4; ++j4) {
@@ -623,12 +639,12 @@ __global__ void k_b_pad_out(const float* __restrict__ Kp, const float* __restric
   V[e] = Vp[int64_t(c) * ldk + r];
 }
 
-template <int P>
+template <int P, bool VS>
 size_t block_smem(int ldk) {
-  return (2 * size_t(P) * ldk + 4 * size_t(P) * P) * sizeof(float);
+  return ((VS ? 2 : 1) * size_t(P) * ldk + 4 * size_t(P) * P) * sizeof(float);
 }
 
-template <int P>
+template <int P, bool VS>
 bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats, float* ms_out, int* sweeps) {
   cudaStream_t st = hc->stream;
   constexpr int B = P / 2;
@@ -636,13 +652,13 @@ bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats,
   if (nb & 1) ++nb;
   if (nb < 2) nb = 2;
   const int ldk = (n + 3) / 4 * 4;
-  const size_t smem = block_smem<P>(ldk);
+  const size_t smem = block_smem<P, VS>(ldk);
   int max_smem = 0;
   CK(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, hc->device));
   if (smem > size_t(max_smem)) return false;
-  allow_max_dynamic_smem((const void*)k_jacobi_block<P>);
+  allow_max_dynamic_smem((const void*)k_jacobi_block<P, VS>);
   int occ = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi_block<P>, BT, smem));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi_block<P, VS>, BT, smem));
   const int grid = nb / 2;
   if (occ < 1 || int64_t(occ) * hc->num_sms < grid) return false;
 
@@ -679,7 +695,7 @@ bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats,
   CK(cudaEventCreate(&ev0));
   CK(cudaEventCreate(&ev1));
   CK(cudaEventRecord(ev0, st));
-  CK(cudaLaunchCooperativeKernel((void*)k_jacobi_block<P>, dim3(grid), dim3(BT), args, smem, st));
+  CK(cudaLaunchCooperativeKernel((void*)k_jacobi_block<P, VS>, dim3(grid), dim3(BT), args, smem, st));
   CK_LAUNCH();
   CK(cudaEventRecord(ev1, st));
   k_b_pad_out<<<unsigned((int64_t(n) * n + 255) / 256), 256, 0, st>>>(Kp.get(), Vp.get(), n, ldk, K, V);
@@ -722,10 +738,12 @@ bool jacobi_svd_block(fastpi_ctx* hc, float* K, float* V, int n, double* sig, in
   if (n < 2) return false;
   float ms = 0;
   int sweeps = 0;
-  // blocks of 8 columns (16-column panels); blocks of 4 when the panels of 8
-  // do not fit in shared memory but a round's block pairs still fit on the SMs
-  bool ok = launch_block<16>(hc, K, V, n, stats, &ms, &sweeps);
-  if (!ok) ok = launch_block<8>(hc, K, V, n, stats, &ms, &sweeps);
+  // blocks of 8 columns (16-column panels) with K and V staged; for wider
+  // cores (n > ~1 790) only K staged, V streamed from L2 (up to n ~ 3 500 and
+  // 152 block pairs per round); then blocks of 4 columns
+  bool ok = launch_block<16, true>(hc, K, V, n, stats, &ms, &sweeps);
+  if (!ok) ok = launch_block<16, false>(hc, K, V, n, stats, &ms, &sweeps);
+  if (!ok) ok = launch_block<8, true>(hc, K, V, n, stats, &ms, &sweeps);
   if (!ok) return false;
   std::vector<JacobiProblem<float>> pr(1);
   pr[0] = JacobiProblem<float>{K, V, n, n, n, n};
