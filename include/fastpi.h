@@ -110,7 +110,10 @@ fastpi_status fastpi_factor(fastpi_t h, int64_t r, double k, fastpi_precision pr
  *   Y: device float64, m x L row-major (ldy >= L), rows in ORIGINAL order.
  *   Z: device float64, n x L row-major (ldz >= L), rows in ORIGINAL order; overwritten.
  * FASTPI_ERR_STATE before a successful fastpi_factor.
- */
+ * The apply synchronises nothing on the host and allocates only
+ * stream-ordered memory on the handle's stream, so it may be recorded into a
+ * CUDA graph (capture on that stream) and replayed for new Y of the same
+ * shape. */
 fastpi_status fastpi_apply(fastpi_t h, const double* Y, int64_t L, int64_t ldy,
                            double* Z, int64_t ldz);
 
