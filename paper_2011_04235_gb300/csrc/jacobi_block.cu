@@ -22,8 +22,10 @@
 // acquire load before it is read).  A device-wide barrier ends each sweep,
 // where the CTAs combine their rotation flags: a sweep in which no pair had
 // |G_pq| / sqrt(G_pp G_qq) above tol leaves K unchanged (converged), and a
-// sweep whose rotations all stayed below 1e-4 ends the iteration (quadratic
-// convergence leaves the next sweep nothing above tol).
+// sweep whose rotations all stayed below 1e-3 ends the iteration (quadratic
+// convergence leaves the next sweep ~1e-6, below tol = sqrt(n) eps32 for the
+// core sizes here; measured on the medium and 200k x 50k workloads: the same
+// residual and orthogonality as with 1e-4, one sweep fewer).
 //
 // K and V are worked on in copies whose leading dimension is a multiple of 4
 // floats (zero rows below n), so every column starts on a 16-byte boundary.
@@ -41,7 +43,7 @@ namespace {
 constexpr int BT = 512;              // threads per CTA (16 warps)
 constexpr int B_MAX_SWEEPS = 30;
 constexpr int INNER_SWEEPS = 1;      // sweeps of the P x P Gram solve per block pair
-constexpr float B_EARLY_OFF = 1e-4f;
+constexpr float B_EARLY_OFF = 1e-3f;
 constexpr unsigned long long B_WAIT_NS = 2000000000ull;   // bound of every wait (2 s)
 
 struct BBar {
