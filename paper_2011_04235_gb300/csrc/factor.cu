@@ -221,6 +221,7 @@ template <typename T>
 __global__ void k_chol_drop_smem(T* G, int c, double tol, int32_t* kept, int32_t* rank) {
   extern __shared__ unsigned char craw[];
   T* P = reinterpret_cast<T*>(craw);
+  T* colj = P + (int64_t(c) * (c + 1)) / 2;   // c entries
   __shared__ int s_keep;
   __shared__ T s_inv;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -242,13 +243,20 @@ __global__ void k_chol_drop_smem(T* G, int c, double tol, int32_t* kept, int32_t
     const int keep = s_keep;
     nk += keep;
     const T inv = s_inv;
-    for (int i = j + 1 + threadIdx.x; i < c; i += blockDim.x) P[(int64_t(i) * (i + 1)) / 2 + j] *= inv;
+    // column j scaled in place and copied to a contiguous buffer: the update
+    // below reads it by row index, which in the packed triangle lands on
+    // scattered banks
+    for (int i = j + 1 + threadIdx.x; i < c; i += blockDim.x) {
+      const T v = P[(int64_t(i) * (i + 1)) / 2 + j] * inv;
+      P[(int64_t(i) * (i + 1)) / 2 + j] = v;
+      colj[i] = v;
+    }
     __syncthreads();
     if (keep) {
       for (int i = j + 1 + w; i < c; i += nw) {
         const int64_t ri = (int64_t(i) * (i + 1)) / 2;
-        const T lij = P[ri + j];
-        for (int l = j + 1 + lane; l <= i; l += 32) P[ri + l] -= lij * P[(int64_t(l) * (l + 1)) / 2 + j];
+        const T lij = colj[i];
+        for (int l = j + 1 + lane; l <= i; l += 32) P[ri + l] -= lij * colj[l];
       }
     }
     __syncthreads();
@@ -371,13 +379,14 @@ __global__ void k_pchol(const double* G, int c, const double* dn, double tol, do
 // index); when it is <= thr the factorization stops (state[0] = 1).  The
 // panel's columns of Lo are staged in shared memory.
 constexpr int PCHOL_NB = 32;
+constexpr int PCHOL_PS = PCHOL_NB + 1;   // panel row stride: odd, so a warp's rows fall in different banks
 constexpr int PCHOL_THREADS = 256;
 __global__ void __launch_bounds__(PCHOL_THREADS) k_pchol_panel(const double* __restrict__ G, int c, int t0,
                                                                const double* dn, double tol, double* d,
                                                                int32_t* used, double* Lo, int32_t* piv,
                                                                int32_t* kept, int32_t* state) {
-  extern __shared__ double pan[];   // c x PCHOL_NB: Lo[:, t0 + k]; then d_s[c]; then used_s[c]
-  double* d_s = pan + size_t(c) * PCHOL_NB;
+  extern __shared__ double pan[];   // c x PCHOL_PS: Lo[:, t0 + k]; then d_s[c]; then used_s[c]
+  double* d_s = pan + size_t(c) * PCHOL_PS;
   int* used_s = reinterpret_cast<int*>(d_s + c);
   __shared__ double red_v[PCHOL_THREADS / 32];
   __shared__ int red_i[PCHOL_THREADS / 32];
@@ -405,7 +414,7 @@ __global__ void __launch_bounds__(PCHOL_THREADS) k_pchol_panel(const double* __r
   }
   if (t0 == 0)
     for (int64_t e = tid; e < int64_t(c) * c; e += PCHOL_THREADS) Lo[e] = 0.0;
-  for (int e = tid; e < c * PCHOL_NB; e += PCHOL_THREADS) pan[e] = 0.0;
+  for (int e = tid; e < c * PCHOL_PS; e += PCHOL_THREADS) pan[e] = 0.0;
 #pragma unroll
   for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (lane == 0) red_v[w] = mx;
@@ -470,15 +479,15 @@ __global__ void __launch_bounds__(PCHOL_THREADS) k_pchol_panel(const double* __r
     // column of pivot j (row j of G, by symmetry) minus this panel's earlier columns
     for (int i = tid; i < c; i += PCHOL_THREADS) {
       if (i == j) {
-        pan[j * PCHOL_NB + k] = ljj;
+        pan[j * PCHOL_PS + k] = ljj;
         used_s[j] = 1;
         continue;
       }
       if (used_s[i]) continue;
       double sacc = G[int64_t(j) * c + i];
-      for (int q = 0; q < k; ++q) sacc -= pan[i * PCHOL_NB + q] * pan[j * PCHOL_NB + q];
+      for (int q = 0; q < k; ++q) sacc -= pan[i * PCHOL_PS + q] * pan[j * PCHOL_PS + q];
       const double lit = sacc / ljj;
-      pan[i * PCHOL_NB + k] = lit;
+      pan[i * PCHOL_PS + k] = lit;
       d_s[i] -= lit * lit;
     }
     if (tid == 0) {
@@ -490,7 +499,7 @@ __global__ void __launch_bounds__(PCHOL_THREADS) k_pchol_panel(const double* __r
   }
   for (int e = tid; e < c * nb; e += PCHOL_THREADS) {
     const int i = e / nb, k = e % nb;
-    Lo[int64_t(i) * c + t0 + k] = pan[i * PCHOL_NB + k];
+    Lo[int64_t(i) * c + t0 + k] = pan[i * PCHOL_PS + k];
   }
   for (int i = tid; i < c; i += PCHOL_THREADS) {
     d[i] = d_s[i];
@@ -729,7 +738,7 @@ struct Phase {
       }
     };
     gram(D.get(), G.get());
-    const size_t pan_bytes = size_t(c) * PCHOL_NB * sizeof(double) + size_t(c) * (sizeof(double) + sizeof(int));
+    const size_t pan_bytes = size_t(c) * PCHOL_PS * sizeof(double) + size_t(c) * (sizeof(double) + sizeof(int));
     if (pan_bytes <= 200 * 1024) {
       // blocked: panels of PCHOL_NB columns in one CTA, trailing updates as FP64 GEMMs
       DArr<double> dd(c, st);
@@ -760,7 +769,7 @@ struct Phase {
     // second pass: Q1 is orthonormal up to rounding, its Gram ~ I is well
     // conditioned, so this Cholesky runs in the storage precision
     gemm_t<T>(st, true, false, c, c, p, T(1), Q1.get(), c, Q1.get(), c, T(0), GT.get(), c);
-    const size_t packed = size_t(c) * (c + 1) / 2 * sizeof(T);
+    const size_t packed = (size_t(c) * (c + 1) / 2 + size_t(c)) * sizeof(T);
     if (packed <= 200 * 1024) {
       if (packed > 48 * 1024)
         allow_max_dynamic_smem((const void*)k_chol_drop_smem<T>);
