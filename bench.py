@@ -178,6 +178,36 @@ def oracle_sample(w, budget_s: float = 60.0):
 
 
 # ----------------------------------------------------------------------------- main
+# DRAM bytes (read + write) of one k_jacobi_block<16, 1> launch of this
+# workload (the first row-phase core, n = 531) from an ncu capture of the
+# current kernel; set to None whenever the kernel changes until it is captured
+# again.
+JACOBI_TRAFFIC_BYTES = 2.289152e6 + 0.556032e6
+JACOBI_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch (n = 531), "
+                         "profiles/k_jacobi_block_medium.md")
+
+
+def bench_config(w):
+    """The workload description shared by both arms of the bench."""
+    cfg = w["cfg"]
+    return {"workload": cfg.name, "m": int(w["m"]), "n": int(w["n"]), "nnz": int(w["col"].size), "r": cfg.r,
+            "k": cfg.k, "L": int(cfg.L), "chunk": CHUNK, "gamma": cfg.gamma, "seed": 0,
+            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
+
+
+def aggregate(world, flops_per_rank, sec_local, pg=None, device=None):
+    """Whole-job throughput of `world` replicas: every rank did flops_per_rank
+    in sec_local seconds; the job took the slowest rank's time (max over the
+    process group).  Returns (GFLOP/s, seconds)."""
+    sec_max = sec_local
+    if pg is not None and world > 1:
+        import torch
+        t = torch.tensor([sec_local], dtype=torch.float64, device=device)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        sec_max = float(t.item())
+    return world * flops_per_rank / sec_max / 1e9, sec_max
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,7 +237,8 @@ def main():
         out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GFLOP/s", "n_gpus": args.gpus,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(secs),
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-               "data": "synthetic", "config": {"workload": w["cfg"].name, "chunk": CHUNK},
+               "data": "synthetic", "config": bench_config(w),
+               "precision": "FP64 CPU oracle (NumPy / SciPy LAPACK)",
                "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
                                 "sample": desc},
                "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -292,12 +323,7 @@ def main():
     info64 = h.info()
 
     sec_mixed = statistics.mean(t_mixed)
-    sec_max = sec_mixed
-    if pg:
-        tt = torch.tensor([sec_mixed], device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        sec_max = float(tt.item())
-    value = world * F / sec_max / 1e9
+    value, sec_max = aggregate(world, F, sec_mixed, pg, dev)
 
     # end to end through the C ABI with host buffers (create + factor + apply_host)
     e2e = None
@@ -333,8 +359,9 @@ def main():
     share = cnt_mixed["jacobi_ms"] / 1000.0 / max(sum(t_mixed), 1e-9)
     roofline = {"kernel": "k_jacobi_block (block one-sided Jacobi core SVD, FP32)", "bound": "alu",
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz "
-                                                "(MEASURED_PEAKS.json)", "time_share": share,
+                "traffic": JACOBI_TRAFFIC_BYTES, "traffic_source": JACOBI_TRAFFIC_SOURCE,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (MEASURED_PEAKS.json)",
+                "time_share": share,
                 "avg_launch_ms": avg_ms, "launches_per_step": cnt_mixed["jacobi_launches"] / args.steps}
 
     cpu = None
@@ -347,12 +374,9 @@ def main():
             "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": 1000 * sec_mixed, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": cfg.name, "m": m, "n": n, "nnz": int(w["col"].size), "r": cfg.r, "k": cfg.k,
-                       "L": int(Yd.shape[1]), "chunk": CHUNK, "gamma": cfg.gamma, "seed": 0,
-                       "precision": "mixed: FP32 storage, TF32 tensor-core products (split hi/lo, 3 passes) "
-                                    "with FP32 accumulation, FP64-accumulated Gram and FP64 Cholesky, "
-                                    "FP32 block-Jacobi core SVD",
-                       "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"},
+            "config": bench_config(w),
+            "precision": "mixed: FP32 storage, TF32 tensor-core products (split hi/lo, 3 passes) with FP32 "
+                         "accumulation, FP64-accumulated Gram and FP64 Cholesky, FP32 block-Jacobi core SVD",
             "mixed": {"seconds": sec_mixed, "gflops": F / sec_mixed / 1e9, "residual": res_mixed,
                       "stage_ms": {k: info[k] for k in info if k.startswith("ms_")}},
             "fp64": {"seconds": statistics.mean(t64), "gflops": F / statistics.mean(t64) / 1e9,
