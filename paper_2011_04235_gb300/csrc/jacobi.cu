@@ -370,18 +370,19 @@ template <typename T> struct Eps;
 template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; };
 template <> struct Eps<float> { static constexpr double v = 1.1920928955078125e-07; };
 
-}  // namespace
 
+// One persistent cooperative launch over `probs`, problem b writing its
+// outputs at sig / perm + out_off[b].
 template <typename T>
-JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& probs, double* sig,
-                               int32_t* perm) {
+JacobiStats run_bucket(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& probs,
+                       const std::vector<int64_t>& out_off, double* sig, int32_t* perm) {
   JacobiStats stats;
   const int nprob = int(probs.size());
   if (nprob == 0) return stats;
   cudaStream_t st = h->stream;
   std::vector<DevProb<T>> dp(nprob);
   std::vector<int64_t> pair_off(nprob), sig_off(nprob);
-  int64_t pairs = 0, soff = 0;
+  int64_t pairs = 0;
   int maxR = 1, maxq = 1, maxp = 1;
   for (int b = 0; b < nprob; ++b) {
     const auto& P = probs[b];
@@ -398,9 +399,8 @@ JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>
     d.pair_off = pairs;
     d.tol_abs2 = 0;
     pair_off[b] = pairs;
-    sig_off[b] = soff;
+    sig_off[b] = out_off[b];
     pairs += d.qe / 2;
-    soff += P.q;
     maxR = std::max(maxR, d.R);
     maxq = std::max(maxq, P.q);
     maxp = std::max(maxp, P.p);
@@ -515,6 +515,52 @@ JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>
   stats.hit_cap = (stat & ST_JACOBI_SWEEPS) != 0;
   return stats;
 }
+
+// Register-tile class of a problem: the kernel variant that holds its longest
+// column (FP32: 8 / 16 / 32 / 44 values per lane, beyond that the two-pass
+// path; FP64: teams of two warps with 8 or 16 values per lane, or four warps).
+template <typename T>
+int tile_class(const JacobiProblem<T>& P) {
+  const int maxdim = std::max(P.p, P.q);
+  if constexpr (sizeof(T) == 4) {
+    const int need = (maxdim + 31) / 32;
+    return need <= 8 ? 0 : need <= 16 ? 1 : need <= 32 ? 2 : need <= 44 ? 3 : 4;
+  } else {
+    return maxdim <= 64 * 8 ? 0 : maxdim <= 64 * 16 ? 1 : 2;
+  }
+}
+
+}  // namespace
+
+// Size-bucketed: the problems are grouped by the register tile their longest
+// column needs, and each group runs in its own persistent launch of the
+// matching kernel variant (a single launch would give every problem the tile
+// of the largest one, and its convergence threshold).
+template <typename T>
+JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& probs, double* sig,
+                               int32_t* perm) {
+  JacobiStats stats;
+  const int nprob = int(probs.size());
+  if (nprob == 0) return stats;
+  constexpr int NCLASS = 5;
+  std::vector<JacobiProblem<T>> bucket[NCLASS];
+  std::vector<int64_t> off[NCLASS];
+  int64_t soff = 0;
+  for (int b = 0; b < nprob; ++b) {
+    const int c = tile_class<T>(probs[b]);
+    bucket[c].push_back(probs[b]);
+    off[c].push_back(soff);
+    soff += probs[b].q;
+  }
+  for (int c = 0; c < NCLASS; ++c) {
+    if (bucket[c].empty()) continue;
+    const JacobiStats js = run_bucket<T>(h, bucket[c], off[c], sig, perm);
+    stats.max_sweeps_used = std::max(stats.max_sweeps_used, js.max_sweeps_used);
+    stats.hit_cap = stats.hit_cap || js.hit_cap;
+  }
+  return stats;
+}
+
 
 template <typename T>
 void jacobi_sort_columns(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& probs, double* sig, int32_t* perm) {
