@@ -670,7 +670,6 @@ struct Phase {
   int cur = 0;
   int64_t k = 0, q = 0;
   double drop_tol;
-  bool use_cluster_svd = true;
   // statistics
   int64_t steps = 0, dropped = 0;
   int sweeps_max = 0;
@@ -799,8 +798,6 @@ struct Phase {
     bool done = false;
     if constexpr (sizeof(T) == 4) {
       done = jacobi_svd_block(h, K.get(), J.get(), int(n), jsig.get(), jperm.get(), &js);
-      if (!done && use_cluster_svd)
-        done = jacobi_svd_cluster(h, K.get(), J.get(), int(n), jsig.get(), jperm.get(), &js);
     }
     if (!done) {
       std::vector<JacobiProblem<T>> pr(1);

@@ -34,17 +34,10 @@ JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>
 template <typename T>
 void jacobi_sort_columns(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& probs, double* sig, int32_t* perm);
 
-// FP32 core SVD of one square n x n column-major K (ld n) inside one
-// thread-block cluster (K resident in distributed shared memory).  Same
-// outputs as jacobi_svd_batched for a single problem (V = J, n x n col-major,
-// ld n).  Returns false, having done nothing, when n is too large for the
-// cluster's shared memory or the device cannot host the cluster; the caller
-// then uses jacobi_svd_batched.
-bool jacobi_svd_cluster(fastpi_ctx* h, float* K, float* V, int n, double* sig, int32_t* perm, JacobiStats* stats);
-
 // FP32 core SVD of one square n x n column-major K (ld n) by block one-sided
 // Jacobi on the whole GPU (column blocks of 4 or 8 columns; one CTA per block
-// pair and round).  Same outputs as jacobi_svd_cluster; returns false, having
+// pair and round).  Same outputs as jacobi_svd_batched for a single problem
+// (V = J, n x n col-major, ld n); returns false, having
 // done nothing, when a block pair's panels do not fit in one CTA's shared
 // memory or the block pairs of a round exceed the co-resident CTAs.
 bool jacobi_svd_block(fastpi_ctx* h, float* K, float* V, int n, double* sig, int32_t* perm, JacobiStats* stats);
