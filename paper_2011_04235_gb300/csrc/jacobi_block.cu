@@ -11,9 +11,8 @@
 //   2. forms the Gram matrix G = X^T X (P x P) with register tiles;
 //   3. runs one cyclic two-sided Jacobi sweep on G (the rotation of a pair
 //      comes from G_pp, G_qq, G_pq exactly as from the column dot products of
-//      scalar one-sided Jacobi), accumulating the rotations in Q (P x P):
-//      for P = 16 the whole CTA updates G and Q in shared memory, for P = 8
-//      one warp keeps them in registers;
+//      scalar one-sided Jacobi), accumulating the rotations in Q (P x P); the
+//      whole CTA updates G and Q in shared memory;
 //   4. writes K_IJ <- X Q and V_IJ <- Y Q.
 // Every block is owned by exactly one CTA per round, so instead of a
 // device-wide barrier per round a CTA waits only for the two CTAs that wrote
@@ -252,88 +251,6 @@ __device__ __forceinline__ float* inner_solve_cta(float* G, float* Gn, float* Q,
   return Q;
 }
 
-// One warp, P <= 8 (the unrolled code of larger P no longer fits the
-// instruction cache): lanes 0..P-1 hold the rows of G, lanes P..2P-1 the rows
-// of Q, in registers; every lane computes all P/2 rotations of a round from
-// shuffled entries of G (the round loop is unrolled, so every column index is
-// a compile-time constant).  Per round: Q <- Q J, G <- J^T G J.
-template <int P>
-__device__ __forceinline__ void inner_solve_regs(const float* G, float* Q, int lane, float tabs, float tol2,
-                                                 float early2, int sweeps, int& rotmax) {
-  constexpr int GS = P;
-  const bool isg = lane < P, isq = lane >= P && lane < 2 * P;
-  const int ri = isg ? lane : (isq ? lane - P : 0);
-  float v[P];
-#pragma unroll
-  for (int c = 0; c < P; ++c) v[c] = isg ? G[ri * GS + c] : ((isq && c == ri) ? 1.f : 0.f);
-  for (int is = 0; is < sweeps; ++is) {
-    int any = 0;
-#pragma unroll
-    for (int ir = 0; ir < P - 1; ++ir) {
-      float cs[P / 2], sn[P / 2];
-#pragma unroll
-      for (int k = 0; k < P / 2; ++k) {
-        int p, q;
-        circle_pair(k, ir, P, p, q);
-        const float al = __shfl_sync(0xffffffffu, v[p], p);
-        const float be = __shfl_sync(0xffffffffu, v[q], q);
-        const float ga = __shfl_sync(0xffffffffu, v[q], p);
-        float c = 1.f, s = 0.f;
-        if (al > tabs && be > tabs && ga * ga > tol2 * al * be) {
-          // t = 2 g sgn(d) / (|d| + sqrt(d^2 + 4 g^2)), d = be - al (smaller root)
-          const float d = be - al;
-          // IEEE square root and division: an approximate c (c^2 + s^2 != 1 by a
-          // few ulp with a fixed sign) would scale V's columns a little on every
-          // one of the thousands of rotations each column receives
-          const float t = 2.f * (d < 0.f ? -ga : ga) / (fabsf(d) + sqrtf(fmaf(d, d, 4.f * ga * ga)));
-          c = 1.f / sqrtf(fmaf(t, t, 1.f));
-          s = c * t;
-          any = 1;
-          rotmax = max(rotmax, ga * ga > early2 * al * be ? 2 : 1);
-        }
-        cs[k] = c;
-        sn[k] = s;
-      }
-      // columns of every row: (x_p, x_q) <- (c x_p - s x_q, s x_p + c x_q)
-#pragma unroll
-      for (int k = 0; k < P / 2; ++k) {
-        int p, q;
-        circle_pair(k, ir, P, p, q);
-        const float x = v[p], y = v[q];
-        v[p] = cs[k] * x - sn[k] * y;
-        v[q] = sn[k] * x + cs[k] * y;
-      }
-      // rows of G: row p <- c row_p - s row_q, row q <- s row_p + c row_q
-      float cc = 1.f, ss = 0.f;
-      int mate = lane;
-#pragma unroll
-      for (int k = 0; k < P / 2; ++k) {
-        int p, q;
-        circle_pair(k, ir, P, p, q);
-        if (isg && ri == p) {
-          cc = cs[k];
-          ss = -sn[k];
-          mate = q;
-        } else if (isg && ri == q) {
-          cc = cs[k];
-          ss = sn[k];
-          mate = p;
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < P; ++c) {
-        const float y = __shfl_sync(0xffffffffu, v[c], mate);
-        v[c] = cc * v[c] + ss * y;
-      }
-    }
-    if (!any) break;
-  }
-  if (isq) {
-#pragma unroll
-    for (int c = 0; c < P; ++c) Q[ri * GS + c] = v[c];
-  }
-}
-
 #ifdef FASTPI_PHASE_CLOCKS
 __device__ long long g_phase_clk[8];
 #define PHASE_MARK(k)                          \
@@ -490,24 +407,12 @@ __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
       for (int e = tid; e < P * P; e += BT) Q[(e / P) * GS + e % P] = (e / P == e % P) ? 1.f : 0.f;
       __syncthreads();
       PHASE_MARK(1);
-      // 3. cyclic two-sided Jacobi on G, rotations accumulated in Q
-      const float* Qf = Q;
-      if constexpr (P <= 8) {
-        if (warp == 0) {
-          int rotmax = 0;
-          inner_solve_regs<P>(G, Q, lane, tabs, tol2, early2, a.inner, rotmax);
-          if (lane == 0 && rotmax) {   // every lane computed every rotation
-            atomicMax(&s_rot, rotmax);
-            s_pair_rot = 1;
-          }
-        }
-      } else {
-        // the pairs inside the blocks in the first round of a sweep (every
-        // block meets its first partner there), only cross pairs afterwards:
-        // every column pair is still visited at least once per sweep
-        Qf = inner_solve_cta<P>(G, Gn, Q, Qn, s_sc, s_so, tid, tabs, tol2, early2, a.inner, rr != 0, &s_rot,
-                                &s_pair_rot);
-      }
+      // 3. cyclic two-sided Jacobi on G, rotations accumulated in Q: the pairs
+      // inside the blocks in the first round of a sweep (every block meets its
+      // first partner there), only cross pairs afterwards, so every column
+      // pair is still visited at least once per sweep
+      const float* Qf = inner_solve_cta<P>(G, Gn, Q, Qn, s_sc, s_so, tid, tabs, tol2, early2, a.inner, rr != 0,
+                                           &s_rot, &s_pair_rot);
       PHASE_MARK(2);
       cp_async_wait<0>();
       __syncthreads();
@@ -741,11 +646,10 @@ bool jacobi_svd_block(fastpi_ctx* hc, float* K, float* V, int n, double* sig, in
   float ms = 0;
   int sweeps = 0;
   // blocks of 8 columns (16-column panels) with K and V staged; for wider
-  // cores (n > ~1 790) only K staged, V streamed from L2 (up to n ~ 3 500 and
-  // 152 block pairs per round); then blocks of 4 columns
+  // cores (n > ~1 790) only K staged, V streamed from L2 (up to n ~ 2 430:
+  // 152 block pairs per round)
   bool ok = launch_block<16, true>(hc, K, V, n, stats, &ms, &sweeps);
   if (!ok) ok = launch_block<16, false>(hc, K, V, n, stats, &ms, &sweeps);
-  if (!ok) ok = launch_block<8, true>(hc, K, V, n, stats, &ms, &sweeps);
   if (!ok) return false;
   std::vector<JacobiProblem<float>> pr(1);
   pr[0] = JacobiProblem<float>{K, V, n, n, n, n};
