@@ -218,3 +218,36 @@ def test_small_workload_residual_close_to_optimal():
     res_full = np.linalg.norm(A @ np.linalg.lstsq(A, w["Y"], rcond=None)[0] - w["Y"])
     assert res_full <= res * (1 + 1e-12)
     assert abs(res - res_r) <= 0.01 * res_r
+
+
+def test_multi_append_row_phase_is_the_running_svd_of_all_rows_of_M():
+    """Reading of Eq. 2 with several appends: the oracle starts the row phase
+    from the s largest block triplets.  Pin: the same result comes out of the
+    incremental SVD run over ALL rows of M = [Sigma1 V1^T ; A21] from an empty
+    state -- the block rows (mutually orthogonal) appended first, in descending
+    sigma, a chunk at a time, then A21 -- truncating to s after every append."""
+    m, n = 300, 90
+    rowptr, col, val = _powerlaw(5, m, n, 1500)
+    A = sp.csr_matrix((val, col, rowptr), shape=(m, n))
+    r, k, chunk = 24, 0.03, 7
+    R = reorder(m, n, rowptr, col, k)
+    _, A11, A21, _ = fastpi.split(A, R)
+    U1, sig1, V1, _ = fastpi.block_svd(A11, R, r, n)
+    S, n1, m2 = sig1.size, R.n1, m - R.m1
+    s = int(min(fastpi.ceil_alpha(n1, r, n), S + m2, n1))
+    assert S > s and m2 > chunk          # the reading applies
+    # the oracle's row phase (factor(): pre-truncation, then the appends)
+    keep = fastpi._truncate(sig1, s)
+    _, sig_a, V_a = fastpi.row_update_chunked(U1[:, keep], sig1[keep], V1[:, keep], A21, s, chunk)
+    # from an empty state over all rows of M (the transposed problem: columns)
+    Uc, sg, W = np.zeros((n1, 0)), np.zeros(0), np.zeros((0, 0))
+    order = fastpi._truncate(sig1, S)
+    cols = V1[:, order] * sig1[order][None, :]
+    for a in range(0, S, chunk):
+        Uc, sg, W = fastpi.brand_append(Uc, sg, W, cols[:, a:a + chunk], s)
+    A21d = A21.toarray()
+    for a in range(0, m2, chunk):
+        Uc, sg, W = fastpi.brand_append(Uc, sg, W, A21d[a:a + chunk].T, s)
+    np.testing.assert_allclose(sg, sig_a, rtol=1e-10, atol=1e-12 * sig_a[0])
+    # the same right subspace
+    np.testing.assert_allclose(np.abs(Uc.T @ V_a), np.eye(s), atol=1e-8)
