@@ -1302,6 +1302,19 @@ struct BlockRendezvous {
     return stats;
   }
 
+  // Registers instance i as taking no part (its thread could not be started)
+  // without waiting for the others.
+  void absent(int i, fastpi_ctx* h) {
+    std::unique_lock<std::mutex> lk(mu);
+    entries[i] = Entry{};
+    if (++arrived == expected) {
+      run(h);
+      done = true;
+      lk.unlock();
+      cv.notify_all();
+    }
+  }
+
   void run(fastpi_ctx* h) {
     std::vector<JacobiProblem<T>> all;
     std::vector<int64_t> off(entries.size(), 0);
@@ -1340,8 +1353,7 @@ void factor_batched_impl(fastpi_ctx* const* hs, int count, const int64_t* r, dou
   Gate pre(concurrency), post(concurrency);
   std::vector<std::thread> th;
   th.reserve(count);
-  for (int i = 0; i < count; ++i) {
-    th.emplace_back([&, i] {
+  auto body = [&](int i) {
       fastpi_ctx* h = hs[i];
       bool arrived = false;
       bool in_pre = true;
@@ -1374,7 +1386,15 @@ void factor_batched_impl(fastpi_ctx* const* hs, int count, const int64_t* r, dou
       } else {
         post.release();
       }
-    });
+  };
+  for (int i = 0; i < count; ++i) {
+    try {
+      th.emplace_back(body, i);
+    } catch (const std::exception& e) {
+      status[i] = FASTPI_ERR_CUDA;
+      msgs[i] = std::string("could not start a host thread: ") + e.what();
+      rv.absent(i, hs[i]);
+    }
   }
   for (auto& t : th) t.join();
 }
