@@ -1150,17 +1150,37 @@ __global__ void k_scale_cols(int64_t rows, int64_t cols, const double* sig, doub
   X[e] = s > tau ? T(double(X[e]) / s) : T(0);
 }
 
+// One warp per row i of A: ||(A Z - Y)[i, :]||^2.  Lane l owns the columns
+// l, l + 32, ... of a pass of RP * 32 columns, with their partial sums in
+// registers, so each nonzero of the row (index and value) is read once per
+// pass and the Z row it selects is read coalesced.
+constexpr int RES_RP = 8;   // columns per lane per pass
 __global__ void k_residual_rows(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                 const double* __restrict__ val, int64_t m, int64_t L, const double* __restrict__ Y,
                                 int64_t ldy, const double* __restrict__ Z, int64_t ldz, double* out) {
   const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= m) return;
+  const int64_t e0 = rowptr[i], e1 = rowptr[i + 1];
   double acc2 = 0;
-  for (int64_t l = lane; l < L; l += 32) {
-    double s = -Y[i * ldy + l];
-    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) s = fma(val[e], Z[int64_t(col[e]) * ldz + l], s);
-    acc2 = fma(s, s, acc2);
+  for (int64_t l0 = 0; l0 < L; l0 += 32 * RES_RP) {
+    double s[RES_RP];
+#pragma unroll
+    for (int u = 0; u < RES_RP; ++u) {
+      const int64_t l = l0 + lane + 32 * u;
+      s[u] = l < L ? -Y[i * ldy + l] : 0.0;
+    }
+    for (int64_t e = e0; e < e1; ++e) {
+      const double v = val[e];
+      const double* zr = Z + int64_t(col[e]) * ldz;
+#pragma unroll
+      for (int u = 0; u < RES_RP; ++u) {
+        const int64_t l = l0 + lane + 32 * u;
+        if (l < L) s[u] = fma(v, zr[l], s[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < RES_RP; ++u) acc2 = fma(s[u], s[u], acc2);
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
