@@ -71,7 +71,10 @@ def flop_model(m, n, nnz_a21, nnz_t, m1, n1, m2, n2, row_off, col_off, r, L, chu
         return min(k, target)
 
     s = int(min(ceil_a(n1), S + m2, n1))
-    s = phase(n1, S, S, m2, s, nnz_a21)
+    # with several appends the row phase starts from the s largest block
+    # triplets (its coefficient matrix keeps the S block rows)
+    k0 = s if (chunk < m2 and S > s) else S
+    s = phase(n1, k0, S, m2, s, nnz_a21)
     F += 2.0 * float(np.sum(mb * sb)) * s            # U_row = bdiag(U1, I) W
     rr = int(min(r, m, s + n2))
     rr = phase(m, s, s, n2, rr, nnz_t)
