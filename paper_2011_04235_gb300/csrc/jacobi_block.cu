@@ -44,6 +44,7 @@ constexpr int B_MAX_SWEEPS = 30;
 constexpr int INNER_SWEEPS = 1;      // sweeps of the P x P Gram solve per block pair
 constexpr float B_EARLY_OFF = 1e-3f;
 constexpr unsigned long long B_WAIT_NS = 2000000000ull;   // bound of every wait (2 s)
+constexpr int VER_STRIDE = 32;   // one 128-byte line per block's round counter (no shared polling lines)
 
 struct BBar {
   unsigned count;
@@ -270,7 +271,7 @@ __device__ long long g_phase_clk[8];
 struct BlkArgs {
   float* K;        // ldk x n column-major: in A (rows >= n zero), out A J
   float* V;        // ldk x n column-major: in I, out J
-  unsigned* ver;   // [nb] rounds completed per block
+  unsigned* ver;   // [nb * VER_STRIDE] rounds completed per block
   int n, ldk;      // ldk: multiple of 4, >= n
   int nb;          // number of column blocks (even; the last may be empty)
   float tol;
@@ -325,10 +326,10 @@ __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
       // wait until the previous round on both blocks is complete
       if (tid == 0) {
         int ok = 1;
-        if (b_ld_acquire(a.ver + bi) < t || b_ld_acquire(a.ver + bj) < t) {
+        if (b_ld_acquire(a.ver + bi * VER_STRIDE) < t || b_ld_acquire(a.ver + bj * VER_STRIDE) < t) {
           const unsigned long long t0 = b_gtimer();
           unsigned spins = 0;
-          while (b_ld_acquire(a.ver + bi) < t || b_ld_acquire(a.ver + bj) < t) {
+          while (b_ld_acquire(a.ver + bi * VER_STRIDE) < t || b_ld_acquire(a.ver + bj * VER_STRIDE) < t) {
             if ((++spins & 63u) == 0 && b_gtimer() - t0 > B_WAIT_NS) {
               atomicOr(a.status, ST_BARRIER_TIMEOUT);
               ok = 0;
@@ -471,8 +472,8 @@ __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
       // hand both blocks to the next round (the release store publishes every
       // write of the CTA, ordered before it by the barrier above)
       if (tid == 0) {
-        b_st_release(a.ver + bi, t + 1u);
-        b_st_release(a.ver + bj, t + 1u);
+        b_st_release(a.ver + bi * VER_STRIDE, t + 1u);
+        b_st_release(a.ver + bj * VER_STRIDE, t + 1u);
       }
       if (rr == a.nb - 2) {
         // end of a sweep: combine the rotation flags of all CTAs
@@ -573,7 +574,7 @@ bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats,
   constexpr int NPART = 128;
   DArr<double> part(NPART, st);
   DArr<int> out(2, st);
-  DArr<unsigned> ver(nb, st);
+  DArr<unsigned> ver(int64_t(nb) * VER_STRIDE, st);
   DArr<float> Kp(int64_t(ldk) * n, st), Vp(int64_t(ldk) * n, st);
   k_b_sumsq_part<<<NPART, 256, 0, st>>>(K, int64_t(n) * n, part.get());
   CK_LAUNCH();
@@ -582,7 +583,7 @@ bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats,
   k_b_pad_in<<<unsigned((int64_t(ldk) * n + 255) / 256), 256, 0, st>>>(K, n, ldk, Kp.get(), Vp.get());
   CK_LAUNCH();
   CK(cudaMemsetAsync(out.get(), 0, 2 * sizeof(int), st));
-  CK(cudaMemsetAsync(ver.get(), 0, nb * sizeof(unsigned), st));
+  CK(cudaMemsetAsync(ver.get(), 0, size_t(nb) * VER_STRIDE * sizeof(unsigned), st));
   CK(cudaMemsetAsync(hc->dstatus.get(), 0, 4, st));
 
   BlkArgs a;
