@@ -185,9 +185,9 @@ def oracle_sample(w, budget_s: float = 60.0):
 # workload (the first row-phase core, n = 531) from an ncu capture of the
 # current kernel; set to None whenever the kernel changes until it is captured
 # again.
-JACOBI_TRAFFIC_BYTES = None
-JACOBI_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch (n = 531), "
-                         "profiles/k_jacobi_block_medium.md")
+JACOBI_TRAFFIC_BYTES = 660.178841e6 * 4.133280e-3
+JACOBI_TRAFFIC_SOURCE = ("ncu dram__bytes.sum.per_second x gpu__time_duration.sum (DRAM read + write) of one "
+                         "launch (n = 531), profiles/k_jacobi_block_medium.md")
 
 
 def bench_config(w):
