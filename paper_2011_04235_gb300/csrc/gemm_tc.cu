@@ -362,19 +362,18 @@ using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, 
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiled encoder() {
-  static EncodeTiled fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // initialised once, thread-safely (concurrent factorizations of a batch
+  // reach their first tensor-core product at the same time)
+  static const EncodeTiled fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiled>(p);
-    else
-      (void)cudaGetLastError();
-  }
+      return reinterpret_cast<EncodeTiled>(p);
+    (void)cudaGetLastError();
+    return EncodeTiled(nullptr);
+  }();
   return fn;
 }
 
@@ -386,7 +385,9 @@ CUtensorMap make_map(const float* p, int64_t rows, int64_t K, int64_t ld, int bo
   const cuuint64_t strides[1] = {cuuint64_t(ld) * sizeof(float)};
   const cuuint32_t box[2] = {cuuint32_t(TC_BK), cuuint32_t(box_rows)};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = encoder()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(p), dims, strides, box,
+  const EncodeTiled enc = encoder();
+  if (!enc) fail(FASTPI_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(p), dims, strides, box,
                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) fail(FASTPI_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(int(r)) + ")");
