@@ -160,14 +160,17 @@ def oracle_sample(w, budget_s: float = 60.0):
     """Time the FP64 CPU oracle, as it stands, on the whole workload: reorder,
     block SVD, row and column updates with the same chunk schedule, and the
     apply.  Returns (GFLOP/s under the bench's flop model, seconds,
-    description, BLAS threads)."""
+    description, BLAS threads, the oracle's singular values, its ||AZ - Y||_F)."""
     from oracle import fastpi as ofp
 
     cfg = w["cfg"]
     t0 = time.perf_counter()
     f = ofp.factor(w["m"], w["n"], w["rowptr"], w["col"], w["val"], cfg.r, cfg.k, chunk_row=CHUNK, chunk_col=CHUNK)
-    ofp.apply(f, w["Y"])
+    Zo = ofp.apply(f, w["Y"])
     secs = time.perf_counter() - t0
+    import scipy.sparse as sp
+    A = sp.csr_matrix((w["val"], w["col"], w["rowptr"]), shape=(w["m"], w["n"]))
+    res_o = float(np.linalg.norm(A @ Zo - w["Y"]))
     reo = f.reo
     F = workload_flops(w, reo.row_order, reo.col_order, reo.row_off, reo.col_off, reo.m1, reo.n1, CHUNK)
     try:
@@ -177,7 +180,7 @@ def oracle_sample(w, budget_s: float = 60.0):
         threads = len(os.sched_getaffinity(0))
     desc = (f"FP64 oracle (NumPy/SciPy LAPACK) on the whole {cfg.name} workload: reorder, block SVD, "
             f"row and column updates with chunk {CHUNK}, apply; flops by the bench's flop model")
-    return F / secs / 1e9, secs, desc, threads
+    return F / secs / 1e9, secs, desc, threads, np.asarray(f.S), res_o
 
 
 # ----------------------------------------------------------------------------- main
@@ -188,6 +191,19 @@ def oracle_sample(w, budget_s: float = 60.0):
 JACOBI_TRAFFIC_BYTES = 660.178841e6 * 4.133280e-3
 JACOBI_TRAFFIC_SOURCE = ("ncu dram__bytes.sum.per_second x gpu__time_duration.sum (DRAM read + write) of one "
                          "launch (n = 531), profiles/k_jacobi_block_medium.md")
+
+
+def factor_accuracy(h):
+    """Deviation of the handle's U and V from orthonormal columns (max |entry|
+    of U^T U - I and V^T V - I) and its singular values (host)."""
+    import torch
+    U, V = h.U(), h.V()
+    eye = torch.eye(U.shape[1], dtype=torch.float64, device=U.device)
+    out = {"UtU_minus_I_max": float((U.T @ U - eye).abs().max().item()),
+           "VtV_minus_I_max": float((V.T @ V - eye).abs().max().item()),
+           "S": np.asarray(h.S())}
+    del U, V
+    return out
 
 
 def bench_config(w):
@@ -233,7 +249,7 @@ def main():
         vals, secs = [], []
         desc, threads = "", 1
         for _ in range(args.steps):
-            g, s, desc, threads = oracle_sample(w, budget_s=20.0)
+            g, s, desc, threads, _, _ = oracle_sample(w, budget_s=20.0)
             vals.append(g)
             secs.append(s)
         v = statistics.mean(vals)
@@ -317,6 +333,7 @@ def main():
     t_mixed, cnt_mixed, clocks = timed("mixed", args.steps, max(args.warmup, 3), sampler)
     res_mixed = h.residual(Yd, Z)
     info = h.info()
+    acc = {"mixed": factor_accuracy(h), "fp64": None}
     ro, co, _, _ = h.perm()
     bro, bco = h.blocks()
     F = workload_flops(w, ro, co, bro, bco, info["m1"], info["n1"], CHUNK)
@@ -324,6 +341,7 @@ def main():
     t64, _, _ = timed("fp64", max(args.fp64_steps, 1), 1)
     res64 = h.residual(Yd, Z)
     info64 = h.info()
+    acc["fp64"] = factor_accuracy(h)
 
     sec_mixed = statistics.mean(t_mixed)
     value, sec_max = aggregate(world, F, sec_mixed, pg, dev)
@@ -369,8 +387,15 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        g, s, desc, threads = oracle_sample(w, budget_s=20.0)
+        g, s, desc, threads, S_o, res_o = oracle_sample(w, budget_s=20.0)
         cpu = {"value": g, "unit": "GFLOP/s", "cores": threads, "kind": "oracle", "sample": desc, "seconds": s}
+        for form, res in (("mixed", res_mixed), ("fp64", res64)):
+            S_g = acc[form].pop("S")
+            acc[form]["sigma_rel_err_vs_oracle"] = (float(np.linalg.norm(S_g - S_o) / np.linalg.norm(S_o))
+                                                    if S_g.size == S_o.size else None)
+            acc[form]["residual_gap_vs_oracle"] = abs(res - res_o) / res_o
+    for form in acc:
+        acc[form].pop("S", None)
 
     if rank == 0:
         out = {
@@ -389,6 +414,7 @@ def main():
             "flops_per_step": F,
             "reorder": {k: info[k] for k in ("m1", "n1", "m2", "n2", "num_blocks", "iterations", "S", "s_row",
                                                "rank", "row_chunks", "col_chunks", "jacobi_sweeps_max")},
+            "accuracy": acc,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
