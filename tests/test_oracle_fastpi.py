@@ -22,7 +22,7 @@ import scipy.sparse as sp
 
 import workloads
 from oracle import fastpi, pinv
-from oracle.reorder import reorder
+from oracle.reorder import Reordering, reorder
 
 
 def _dense(m, n, rowptr, col, val):
@@ -159,6 +159,57 @@ def test_block_truncation_rule():
     assert np.array_equal(si, expect)
 
 
+def test_block_ranks_hand_computed():
+    """Eq. 1 on hand-made blocks of A11 (m_1i x n_1i): 2 x 10, 10 x 2, 3 x 3,
+    4 x 5, 1 x 1, with alpha = r / n = 21 / 42 = 0.5.  The kept rank of a block
+    is set by its column count: ceil(0.5 * 10) = 5 capped by 2 rows -> 2;
+    ceil(0.5 * 2) = 1; ceil(1.5) = 2; ceil(2.5) = 3; ceil(0.5) = 1.  Each block
+    keeps its s_i largest singular values (LAPACK on the block alone) with
+    singular vectors supported on the block's rows and columns."""
+    shapes = [(2, 10), (10, 2), (3, 3), (4, 5), (1, 1)]
+    expect = [2, 1, 2, 3, 1]
+    ro = np.concatenate([[0], np.cumsum([a for a, _ in shapes])])
+    co = np.concatenate([[0], np.cumsum([b for _, b in shapes])])
+    m1, n1 = int(ro[-1]), int(co[-1])
+    rng = np.random.default_rng(3)
+    A11 = np.zeros((m1, n1))
+    for b, (p, q) in enumerate(shapes):
+        A11[ro[b]:ro[b + 1], co[b]:co[b + 1]] = rng.uniform(0.1, 1.0, (p, q))
+    R = Reordering(m1, n1, np.arange(m1), np.arange(n1), ro, co, m1, n1, 1, [])
+    U1, s1, V1, si = fastpi.block_svd(sp.csr_matrix(A11), R, r=21, n=42)
+    assert si.tolist() == expect
+    pos = np.concatenate([[0], np.cumsum(expect)])
+    for b in range(len(shapes)):
+        blk = A11[ro[b]:ro[b + 1], co[b]:co[b + 1]]
+        sv = np.linalg.svd(blk, compute_uv=False)[:expect[b]]
+        np.testing.assert_allclose(s1[pos[b]:pos[b + 1]], sv, rtol=1e-13)
+        outside_r = np.delete(U1[:, pos[b]:pos[b + 1]], np.s_[ro[b]:ro[b + 1]], axis=0)
+        outside_c = np.delete(V1[:, pos[b]:pos[b + 1]], np.s_[co[b]:co[b + 1]], axis=0)
+        assert not outside_r.any() and not outside_c.any()
+        Ub = U1[ro[b]:ro[b + 1], pos[b]:pos[b + 1]]
+        Vb = V1[co[b]:co[b + 1], pos[b]:pos[b + 1]]
+        np.testing.assert_allclose(blk @ Vb, Ub * sv[None, :], atol=1e-13)
+
+
+def test_alpha_above_one_caps_the_phase_ranks():
+    """r = 2n (alpha = 2) on a matrix of full column rank: no phase can hold
+    more triplets than its matrix has columns, so the row phase keeps
+    rank [A11; A21] = n1 triplets (M has n1 columns) and the result has
+    rank(A) = n, with A's singular values exactly (LAPACK on the dense A)."""
+    m, n = 90, 30
+    rowptr, col, val = _powerlaw(17, m, n, 400)
+    A = _dense(m, n, rowptr, col, val)
+    A[np.arange(n), np.arange(n)] += 1.0          # full column rank
+    rowptr, col, val = _csr(A)
+    f = fastpi.factor(m, n, rowptr, col, val, r=2 * n, k=0.05, chunk_row=5, chunk_col=3)
+    Ap = A[f.reo.row_order][:, f.reo.col_order]
+    n1 = f.reo.n1
+    assert np.linalg.matrix_rank(Ap[:, :n1]) == n1
+    assert f.s_row == n1
+    assert f.rank == n and f.S.size == n
+    np.testing.assert_allclose(f.S, np.linalg.svd(A, compute_uv=False), rtol=1e-12)
+
+
 @pytest.mark.parametrize("alpha_r", [5, 12, 25])
 def test_single_shot_equals_one_chunk(alpha_r):
     """Eqs. 2 and 3 as printed (dense M, N) equal the incremental form with one chunk."""
@@ -251,3 +302,15 @@ def test_multi_append_row_phase_is_the_running_svd_of_all_rows_of_M():
     np.testing.assert_allclose(sg, sig_a, rtol=1e-10, atol=1e-12 * sig_a[0])
     # the same right subspace
     np.testing.assert_allclose(np.abs(Uc.T @ V_a), np.eye(s), atol=1e-8)
+    # and factor() itself (its own start of the row phase): its result is the
+    # empty-state row phase above followed by the column phase (Eq. 3).  The
+    # coefficients W index the rows of M: the S block rows in the order they
+    # were appended, then the rows of A21, so U_row = bdiag(U1, I) W.
+    f = fastpi.factor(m, n, rowptr, col, val, r, k, chunk_row=chunk, chunk_col=chunk)
+    Urow = np.vstack([U1[:, order] @ W[:S], W[S:]])
+    _, _, _, T = fastpi.split(A, R)
+    rr = int(min(r, m, s + R.n2))
+    U_e, S_e, V_e = fastpi.col_update_chunked(Urow, sg, Uc, T, rr, chunk)
+    np.testing.assert_allclose(f.S, S_e, rtol=1e-10, atol=1e-12 * S_e[0])
+    np.testing.assert_allclose(np.abs(U_e[R.row_pos].T @ f.U), np.eye(rr), atol=1e-7)
+    np.testing.assert_allclose(np.abs(V_e[R.col_pos].T @ f.V), np.eye(rr), atol=1e-7)

@@ -31,7 +31,7 @@ def _csr_from_edges(m, n, edges):
     return rowptr, col
 
 
-@pytest.mark.parametrize("name", ["fig2_toy.json", "star.json"])
+@pytest.mark.parametrize("name", ["fig2_toy.json", "star.json", "one_side_stop.json"])
 def test_golden_hand_derived(name):
     g = json.load(open(os.path.join(GOLD, name)))
     rowptr, col = _csr_from_edges(g["m"], g["n"], g["edges_row_col"])
