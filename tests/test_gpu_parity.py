@@ -62,7 +62,7 @@ def test_reorder_bitexact_tiny(seed):
     assert bro.tolist() == R.row_off.tolist() and bco.tolist() == R.col_off.tolist()
 
 
-@pytest.mark.parametrize("name", ["fig2_toy.json", "star.json"])
+@pytest.mark.parametrize("name", ["fig2_toy.json", "star.json", "one_side_stop.json"])
 def test_reorder_golden(name):
     g = json.load(open(os.path.join(GOLD, name)))
     m, n = g["m"], g["n"]
@@ -78,6 +78,7 @@ def test_reorder_golden(name):
     assert ro.tolist() == g["row_order"] and co.tolist() == g["col_order"]
     bro, bco = h.blocks()
     assert bro.tolist() == g["row_off"] and bco.tolist() == g["col_off"]
+    assert h.info()["iterations"] == g["iterations"]
 
 
 @pytest.mark.parametrize("name", ["small", "medium"])
