@@ -126,14 +126,22 @@ fastpi_status fastpi_apply_host(fastpi_t h, const double* Y, int64_t L, int64_t 
 /*
  * fastpi_apply_csr -- as fastpi_apply for a sparse label matrix Y (m x L, CSR,
  * device pointers: yrowptr int64[m+1], ycol int32[nnz_y] in [0, L), yval
- * float64[nnz_y]).  Z: device float64 n x L row-major.
+ * float64[nnz_y]).  Z: device float64 n x L row-major (ldz >= L), rows in
+ * ORIGINAL order; overwritten.  Y is checked as fastpi_create checks A:
+ * FASTPI_ERR_CSR when yrowptr does not run from 0 to nnz_y without
+ * decreasing, or a row's labels are not strictly increasing within [0, L)
+ * (Z is then untouched).  FASTPI_ERR_ARG for L or nnz_y of 2^31 - 1 or more;
+ * FASTPI_ERR_STATE before a successful fastpi_factor.  The check reads Y back,
+ * so the call synchronises the handle's stream.
  */
 fastpi_status fastpi_apply_csr(fastpi_t h, int64_t L, int64_t nnz_y, const int64_t* yrowptr,
                                const int32_t* ycol, const double* yval, double* Z, int64_t ldz);
 
 /* fastpi_residual -- ||A Z - Y||_F in FP64 (Application 1's objective).
  * Y: device m x L (ldy), Z: device n x L (ldz), both rows in ORIGINAL order.
- * *out: host double. */
+ * *out: host double; the call synchronises the handle's stream.  Errors:
+ * FASTPI_ERR_ARG (null pointers, ldy or ldz < L), FASTPI_ERR_STATE (a handle
+ * made from factors has no matrix). */
 fastpi_status fastpi_residual(fastpi_t h, const double* Y, int64_t L, int64_t ldy,
                               const double* Z, int64_t ldz, double* out);
 
@@ -146,7 +154,9 @@ fastpi_status fastpi_residual(fastpi_t h, const double* Y, int64_t L, int64_t ld
  * real-time loops.  Its scratch is a static device array of
  * FASTPI_NOALLOC_MAX_ROWS + 1 doubles (8 MiB) that every GPU loading the
  * library keeps until the process exits.
- *   A: device CSR (rowptr int64[m+1], colind int32[nnz], val float64[nnz]), m x n.
+ *   A: device CSR (rowptr int64[m+1], colind int32[nnz], val float64[nnz]), m x n;
+ *      not checked here (checking would need a read-back): it must pass the
+ *      checks fastpi_create makes, else the result is undefined.
  *   Y: device m x L (ldy), Z: device n x L (ldz), row-major.  *out: host double.
  *   cuda_stream: the stream to run on (NULL = legacy default stream).
  * FASTPI_ERR_ARG when m > FASTPI_NOALLOC_MAX_ROWS or an argument is invalid.

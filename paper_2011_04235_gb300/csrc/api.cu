@@ -139,15 +139,20 @@ fastpi_status fastpi_factor_batched(fastpi_t* hs, int count, const int64_t* r, d
     g_create_error = e.msg;
     return e.status;
   }
-  std::vector<fastpi_status> st(count, FASTPI_OK);
-  std::vector<std::string> msg(count);
+  std::vector<fastpi_status> st;
+  std::vector<std::string> msg;
   try {
+    st.assign(count, FASTPI_OK);
+    msg.resize(count);
     CK(cudaSetDevice(hs[0]->device));
     fastpi::factor_batched(hs, count, r, k, prec, chunk_row, chunk_col, concurrency > 0 ? concurrency : 4,
                            st.data(), msg.data());
   } catch (const Error& e) {
     g_create_error = e.msg;
     return e.status;
+  } catch (const std::exception& e) {   // e.g. a host thread that could not start
+    g_create_error = e.what();
+    return FASTPI_ERR_CUDA;
   }
   fastpi_status first = FASTPI_OK;
   for (int i = 0; i < count; ++i) {
@@ -260,6 +265,8 @@ fastpi_status fastpi_apply_csr(fastpi_t h, int64_t L, int64_t nnz_y, const int64
   use_device(h);
   require_factored(h);
   require(L >= 0 && ldz >= L && nnz_y >= 0, FASTPI_ERR_ARG, "need L >= 0, ldz >= L, nnz_y >= 0");
+  require(L < (int64_t(1) << 31) - 1 && nnz_y < (int64_t(1) << 31) - 1, FASTPI_ERR_ARG,
+          "L and nnz_y must fit in int32");
   require(L == 0 || (yrowptr && Z && (nnz_y == 0 || (ycol && yval))), FASTPI_ERR_ARG, "null pointer");
   apply_csr(h, L, nnz_y, yrowptr, ycol, yval, Z, ldz);
   API_END(h)
@@ -272,6 +279,7 @@ fastpi_status fastpi_residual(fastpi_t h, const double* Y, int64_t L, int64_t ld
   use_device(h);
   require(out != nullptr, FASTPI_ERR_ARG, "out is NULL");
   require(L >= 0 && ldy >= L && ldz >= L, FASTPI_ERR_ARG, "need L >= 0, ldy >= L, ldz >= L");
+  require(L == 0 || (Y && Z), FASTPI_ERR_ARG, "null Y or Z");
   require(h->has_matrix, FASTPI_ERR_STATE, "handle made from factors has no matrix");
   *out = residual(h, Y, L, ldy, Z, ldz);
   API_END(h)

@@ -1590,7 +1590,11 @@ void apply_csr(fastpi_ctx* h, int64_t L, int64_t nnz_y, const int64_t* yrowptr, 
     tmp_ctx.rowptr.b.p = const_cast<int64_t*>(yrowptr);
     tmp_ctx.col.b.p = const_cast<int32_t*>(ycol);
     tmp_ctx.val.b.p = const_cast<double*>(yval);
+    tmp_ctx.dstatus = DArr<unsigned>(1, st);
     try {
+      // the CSC build indexes by label and row: check Y first, as A is
+      // checked when the handle is made
+      validate_csr(&tmp_ctx);
       build_csc(&tmp_ctx);
     } catch (...) {
       tmp_ctx.rowptr.b.p = nullptr;

@@ -175,6 +175,19 @@ def _ptr(t: torch.Tensor) -> int:
     return t.data_ptr()
 
 
+def _dense_dev(t, rows: int, name: str, writable: bool = False) -> torch.Tensor:
+    """A CUDA float64 matrix with `rows` rows and unit column stride (copied
+    to that layout if needed; an output must already have it)."""
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.dim() == 2
+            and t.shape[0] == rows):
+        raise ValueError(f"{name} must be a 2-D CUDA float64 tensor with {rows} rows")
+    if t.stride(1) != 1 or (t.shape[0] > 1 and t.stride(0) < t.shape[1]):
+        if writable:
+            raise ValueError(f"{name} must be row-major (unit column stride)")
+        t = t.contiguous()
+    return t
+
+
 def _stream_ptr(device) -> int:
     return torch.cuda.current_stream(device).cuda_stream
 
@@ -271,10 +284,14 @@ class FastPI:
         return self
 
     def apply(self, Y: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
-        assert Y.is_cuda and Y.dtype == torch.float64 and Y.dim() == 2 and Y.shape[0] == self.m
-        Y = Y if Y.stride(1) == 1 else Y.contiguous()
+        Y = _dense_dev(Y, self.m, "Y")
         L = Y.shape[1]
-        Z = out if out is not None else torch.empty((self.n, L), dtype=torch.float64, device=Y.device)
+        if out is None:
+            Z = torch.empty((self.n, L), dtype=torch.float64, device=Y.device)
+        else:
+            Z = _dense_dev(out, self.n, "out", writable=True)
+            if Z.shape[1] != L:
+                raise ValueError(f"out must have {L} columns")
         with torch.cuda.device(self.device):
             _check(lib().fastpi_apply(self._h, _ptr(Y), L, Y.stride(0), _ptr(Z), Z.stride(0)), self._h)
         return Z
@@ -288,6 +305,17 @@ class FastPI:
         return Z
 
     def apply_csr(self, L: int, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor) -> torch.Tensor:
+        """Z = A^+ Y for a sparse label matrix Y (m x L, CSR on the device:
+        rowptr int64[m+1], col int32 labels strictly increasing per row,
+        val float64); the library checks Y and raises FastPIError on a
+        malformed one."""
+        if not all(isinstance(t, torch.Tensor) and t.is_cuda for t in (rowptr, col, val)):
+            raise ValueError("rowptr, col and val must be CUDA tensors")
+        if rowptr.numel() != self.m + 1 or col.numel() != val.numel():
+            raise ValueError(f"need rowptr of {self.m + 1} entries and col, val of equal length")
+        rowptr = rowptr.to(torch.int64).contiguous()
+        col = col.to(torch.int32).contiguous()
+        val = val.to(torch.float64).contiguous()
         Z = torch.empty((self.n, L), dtype=torch.float64, device=self.device)
         with torch.cuda.device(self.device):
             _check(lib().fastpi_apply_csr(self._h, int(L), int(col.numel()), _ptr(rowptr), _ptr(col), _ptr(val),
@@ -295,6 +323,11 @@ class FastPI:
         return Z
 
     def residual(self, Y: torch.Tensor, Z: torch.Tensor) -> float:
+        """||A Z - Y||_F in FP64 (Y: m x L, Z: n x L, CUDA float64)."""
+        Y = _dense_dev(Y, self.m, "Y")
+        Z = _dense_dev(Z, self.n, "Z")
+        if Y.shape[1] != Z.shape[1]:
+            raise ValueError("Y and Z must have the same number of columns")
         out = C.c_double()
         with torch.cuda.device(self.device):
             _check(lib().fastpi_residual(self._h, _ptr(Y), Y.shape[1], Y.stride(0), _ptr(Z), Z.stride(0),

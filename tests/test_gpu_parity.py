@@ -164,6 +164,28 @@ def test_apply_variants_agree():
     assert rel(Zc, Zd) <= 1e-12
 
 
+def test_apply_csr_rejects_malformed_labels():
+    """A label CSR with a label outside [0, L), or a row whose labels are not
+    increasing, is refused with FASTPI_ERR_CSR before anything reads Y by
+    label, and the handle keeps working."""
+    fp = binding()
+    w = workloads.make("small")
+    cfg = w["cfg"]
+    h = _handle((w["m"], w["n"], w["rowptr"], w["col"], w["val"])).factor(cfg.r, cfg.k, "fp64", 64, 64)
+    rp, cl, vl = workloads.labels_csr(w["m"], cfg.L, cfg.p, np.random.default_rng(5))
+    good = h.apply_csr(cfg.L, *(torch.from_numpy(a).to(DEV) for a in (rp, cl, vl))).cpu().numpy()
+    bad_range = cl.copy()
+    bad_range[7] = cfg.L                            # label L in an L-label matrix
+    bad_order = cl.copy()
+    bad_order[0], bad_order[1] = cl[1], cl[0]       # row 0 decreasing
+    for bad in (bad_range, bad_order):
+        with pytest.raises(fp.FastPIError) as e:
+            h.apply_csr(cfg.L, *(torch.from_numpy(a).to(DEV) for a in (rp, bad, vl)))
+        assert e.value.status == 2
+    again = h.apply_csr(cfg.L, *(torch.from_numpy(a).to(DEV) for a in (rp, cl, vl))).cpu().numpy()
+    assert np.array_equal(again, good)
+
+
 def test_getters_original_order():
     """U and V come back in the caller's row / column order: A ~ U S V^T."""
     w = workloads.make("small")
