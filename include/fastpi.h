@@ -149,20 +149,20 @@ fastpi_status fastpi_residual(fastpi_t h, const double* Y, int64_t L, int64_t ld
  * fastpi_residual_noalloc -- |A Z - Y|_F in FP64, like fastpi_residual, but
  * without a handle and without allocating anything.  The paper has no
  * counterpart: this serves callers that cannot allocate device memory when
- * they need the residual -- code running while a CUDA graph is captured, code
- * under a fixed memory budget with the allocator locked, allocation-free
- * real-time loops.  Its scratch is a static device array of
+ * they need the residual -- code under a fixed memory budget with the
+ * allocator locked, allocation-free real-time loops.  Its scratch is a static device array of
  * FASTPI_NOALLOC_MAX_ROWS + 1 doubles (8 MiB) that every GPU loading the
  * library keeps until the process exits.
  *   A: device CSR (rowptr int64[m+1], colind int32[nnz], val float64[nnz]), m x n;
- *      not checked here (checking would need a read-back): it must pass the
- *      checks fastpi_create makes, else the result is undefined.
+ *      not checked here (that would be a second pass over A on every call):
+ *      it must pass the checks fastpi_create makes, else the result is
+ *      undefined.
  *   Y: device m x L (ldy), Z: device n x L (ldz), row-major.  *out: host double.
  *   cuda_stream: the stream to run on (NULL = legacy default stream).
  * FASTPI_ERR_ARG when m > FASTPI_NOALLOC_MAX_ROWS or an argument is invalid.
- * The first call on each device looks up the scratch address on that device
- * (make it before any stream capture).  All calls share the scratch, so calls
- * that overlap on the GPU race; each call overwrites all the scratch it reads.
+ * The first call on each device looks up the scratch address on that device.
+ * All calls share the scratch, so calls that overlap on the GPU race; each
+ * call overwrites all the scratch it reads.
  * The call synchronises the stream to return the value.
  */
 #define FASTPI_NOALLOC_MAX_ROWS (1 << 20)

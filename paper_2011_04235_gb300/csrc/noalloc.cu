@@ -1,10 +1,9 @@
 // fastpi_residual_noalloc: |A Z - Y|_F without any device allocation.
 //
 // Some callers cannot call cudaMalloc (or anything that allocates) at the
-// moment they need this number: code that runs while a CUDA graph is being
-// captured, code that works under a fixed, pre-reserved memory budget with the
-// allocator locked, and allocation-free real-time loops that must not touch
-// the allocator.  For them this entry point keeps its scratch (one FP64
+// moment they need this number: code that works under a fixed, pre-reserved
+// memory budget with the allocator locked, and allocation-free real-time loops
+// that must not touch the allocator.  For them this entry point keeps its scratch (one FP64
 // partial sum per row of A, plus the total) in a file-scope __device__ array of
 // FASTPI_NOALLOC_MAX_ROWS + 1 doubles (8 MiB).  Every GPU that loads the
 // library holds that array until the process exits.
@@ -13,8 +12,7 @@
 // address, so the host never passes it to a kernel: on the first call on each
 // device (with that device current) the entry point looks the address up with
 // cudaGetSymbolAddress, checks the result, caches it per device and passes it
-// to the kernels.  That first call should therefore come before any stream
-// capture.  All calls share the array: calls that overlap on the GPU (for
+// to the kernels.  All calls share the array: calls that overlap on the GPU (for
 // example on two streams) race on it.  Every call overwrites all the entries
 // it reads, so nothing has to be cleared between calls.
 #include <cmath>

@@ -1,8 +1,8 @@
 """fastpi_residual_noalloc against fastpi_residual.
 
 The no-allocation entry point exists for callers that cannot allocate device
-memory when they need the residual (inside CUDA graph capture, under a locked
-memory budget, in allocation-free loops); it keeps its scratch in a static
+memory when they need the residual (under a locked memory budget, in
+allocation-free loops); it keeps its scratch in a static
 device array.  This test calls it through the C ABI twice in a row (the second
 call finds the previous call's scratch contents) and checks both results
 against the handle-based fastpi_residual, with the relative tolerance the
