@@ -85,7 +85,7 @@ fastpi_status fastpi_create(fastpi_t* out, int64_t m, int64_t n, int64_t nnz,
                             int ptrs_on_device, void* cuda_stream);
 
 /*
- * fastpi_factor -- Algorithm 1, lines 1-4: reorder A by Algorithm 2 (hub ratio
+ * fastpi_factor -- Algorithm 1 up to the solve: reorder A by Algorithm 2 (hub ratio
  * k in (0,1)), SVD of the block-diagonal A11 (Eq. 1, per-block rank
  * s_i = min(ceil(alpha n_1i), m_1i, n_1i)), row incremental update with A21
  * (Eq. 2, rank s = min(ceil(alpha n1), S + m2, n1)) and column incremental
@@ -170,7 +170,7 @@ fastpi_status fastpi_residual_noalloc(int64_t m, int64_t n, const int64_t* rowpt
                                       const double* val, const double* Y, int64_t L, int64_t ldy,
                                       const double* Z, int64_t ldz, double* out, void* cuda_stream);
 
-/* Many independent factorizations (Algorithm 1, lines 1-4, once per handle):
+/* Many independent factorizations (Algorithm 1 up to the solve, once per handle):
  * handle i is factored at target rank r[i] with the common hub ratio k,
  * precision and chunk sizes, exactly as fastpi_factor would (same results).
  * The A11 block SVDs (Eq. 1) of ALL handles run in one persistent batched

@@ -223,7 +223,7 @@ def col_update_chunked(Urow, sig_row, Vrow, T: sp.csr_matrix, r: int, chunk: int
 def factor(m: int, n: int, rowptr, col, val, r: int, k: float,
            chunk_row: int | None = None, chunk_col: int | None = None,
            single_shot: bool = False) -> Factorization:
-    """Algorithm 1 (lines 1-4): reorder, SVD of A11, row update, column update.
+    """Algorithm 1 up to the solve: reorder, SVD of A11, row update, column update.
 
     ``chunk_row`` / ``chunk_col``: border rows / columns appended per
     incremental step (None or 0: the whole border at once).  ``single_shot``
