@@ -2,6 +2,7 @@
 GPU, and exports every function that include/fastpi.h declares (no compute
 call is made)."""
 import ctypes
+import numpy as np
 import os
 import re
 
@@ -36,3 +37,19 @@ def test_last_error_without_handle():
     from paper_2011_04235_gb300 import fastpi
     # a NULL handle is accepted and returns a (possibly empty) message
     assert isinstance(fastpi.lib().fastpi_last_error(None), bytes)
+
+
+def test_binding_rejects_bad_dense_arguments():
+    """The binding checks tensors before any pointer reaches the library: a
+    host tensor, a non-tensor or a tensor on a non-CUDA device is refused with
+    ValueError (no GPU needed: nothing is called)."""
+    import pytest
+    import torch
+    from paper_2011_04235_gb300 import fastpi
+    with pytest.raises(ValueError):
+        fastpi._dense_dev(torch.zeros(4, 3, dtype=torch.float64), 4, "Y")         # host tensor
+    with pytest.raises(ValueError):
+        fastpi._dense_dev(np.zeros((4, 3)), 4, "Y")                              # not a tensor
+    meta = torch.empty(4, 3, dtype=torch.float64, device="meta")
+    with pytest.raises(ValueError):
+        fastpi._dense_dev(meta, 4, "Y")                                          # not CUDA either
