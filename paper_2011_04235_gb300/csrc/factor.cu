@@ -1335,17 +1335,25 @@ struct BlockRendezvous {
     }
   }
 
+  // Never throws: a failure is recorded in `failed` / `error` for every
+  // instance that took part.
   void run(fastpi_ctx* h) {
     std::vector<JacobiProblem<T>> all;
     std::vector<int64_t> off(entries.size(), 0);
     int64_t tot = 0;
-    for (size_t i = 0; i < entries.size(); ++i) {
-      off[i] = tot;
-      if (!entries[i].probs) continue;
-      for (const auto& pr : *entries[i].probs) {
-        all.push_back(pr);
-        tot += pr.q;
+    try {
+      for (size_t i = 0; i < entries.size(); ++i) {
+        off[i] = tot;
+        if (!entries[i].probs) continue;
+        for (const auto& pr : *entries[i].probs) {
+          all.push_back(pr);
+          tot += pr.q;
+        }
       }
+    } catch (const std::exception& e) {
+      failed = true;
+      error = Error{FASTPI_ERR_OOM, e.what()};
+      return;
     }
     try {
       sig_all = DArr<double>(std::max<int64_t>(tot, 1), h->stream);
@@ -1355,6 +1363,10 @@ struct BlockRendezvous {
     } catch (const Error& e) {
       failed = true;
       error = e;
+      return;
+    } catch (const std::exception& e) {   // never leave the waiting instances without `done`
+      failed = true;
+      error = Error{FASTPI_ERR_CUDA, e.what()};
       return;
     }
     for (size_t i = 0; i < entries.size(); ++i) {
@@ -1376,7 +1388,7 @@ void factor_batched_impl(fastpi_ctx* const* hs, int count, const int64_t* r, dou
   auto body = [&](int i) {
       fastpi_ctx* h = hs[i];
       bool arrived = false;
-      bool in_pre = true;
+      bool in_pre = true, in_post = false;
       pre.acquire();
       try {
         CK(cudaSetDevice(h->device));
@@ -1386,6 +1398,7 @@ void factor_batched_impl(fastpi_ctx* const* hs, int count, const int64_t* r, dou
           arrived = true;
           JacobiStats js = rv.arrive(i, h, &probs, &sig, &perm);
           post.acquire();
+          in_post = true;
           return js;
         };
         factor_into<T>(h, r[i], k, prec, chunk_row, chunk_col, bs);
@@ -1398,13 +1411,12 @@ void factor_batched_impl(fastpi_ctx* const* hs, int count, const int64_t* r, dou
         msgs[i] = e.what();
       }
       if (in_pre) pre.release();
+      if (in_post) post.release();
       if (!arrived) {
         try {
           rv.arrive(i, h, nullptr, nullptr, nullptr);
         } catch (...) {
         }
-      } else {
-        post.release();
       }
   };
   for (int i = 0; i < count; ++i) {
