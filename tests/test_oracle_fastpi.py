@@ -210,6 +210,23 @@ def test_alpha_above_one_caps_the_phase_ranks():
     np.testing.assert_allclose(f.S, np.linalg.svd(A, compute_uv=False), rtol=1e-12)
 
 
+@pytest.mark.parametrize("shape", [(1, 6), (7, 1), (1, 1), (5, 5)])
+@pytest.mark.parametrize("chunk", [None, 1])
+def test_degenerate_shapes_equal_lapack_pinv(shape, chunk):
+    """A single row, a single column, a 1 x 1 and a fully dense matrix, with
+    r = 2n (alpha >= 1): Algorithm 2 leaves A11 empty on one side (m1 = 0 or
+    n1 = 0) or entirely, and the factorization must still give Z = A^+ Y
+    exactly (LAPACK's pinv of the dense A)."""
+    m, n = shape
+    rng = np.random.default_rng(m * 10 + n)
+    A = rng.uniform(0.1, 1.0, shape)
+    rowptr, col, val = _csr(A)
+    f = fastpi.factor(m, n, rowptr, col, val, r=2 * n, k=0.3, chunk_row=chunk, chunk_col=chunk)
+    Y = rng.standard_normal((m, 3))
+    np.testing.assert_allclose(fastpi.apply(f, Y), np.linalg.pinv(A) @ Y, atol=1e-13)
+    np.testing.assert_allclose(f.S, np.linalg.svd(A, compute_uv=False), rtol=1e-13)
+
+
 @pytest.mark.parametrize("alpha_r", [5, 12, 25])
 def test_single_shot_equals_one_chunk(alpha_r):
     """Eqs. 2 and 3 as printed (dense M, N) equal the incremental form with one chunk."""
