@@ -107,10 +107,12 @@ def _parity(m, n, rowptr, col, val, Y, r, k, cr, cc, ztol=1e-9, stol=1e-10):
     inf = h.info()
     if _gap(f) > 1e-8:
         assert rel(Z, Zo) <= ztol, f"Z rel err {rel(Z, Zo):.3e}"
-    # residual through the library equals the dense residual
+    # residual through the library equals the dense residual (when A has full
+    # row rank the system is consistent, A Z = Y, and both are rounding noise:
+    # hence the absolute floor, relative to |Y|)
     A = dense(m, n, rowptr, col, val)
     res = h.residual(Yd, torch.from_numpy(Z).to(DEV))
-    np.testing.assert_allclose(res, np.linalg.norm(A @ Z - Y), rtol=1e-12)
+    np.testing.assert_allclose(res, np.linalg.norm(A @ Z - Y), rtol=1e-12, atol=1e-12 * np.linalg.norm(Y))
     return h, f, inf
 
 
@@ -119,6 +121,29 @@ def test_factor_fp64_small(chunks):
     w = workloads.make("small")
     cfg = w["cfg"]
     _parity(w["m"], w["n"], w["rowptr"], w["col"], w["val"], w["Y"], cfg.r, cfg.k, *chunks)
+
+
+@pytest.mark.parametrize("shape", [(1, 6), (7, 1), (1, 1), (5, 5)])
+@pytest.mark.parametrize("chunks", [(None, None), (1, 1)])
+def test_one_sided_empty_a11(shape, chunks):
+    """Inputs where Algorithm 2 leaves A11 empty on one side or both (a single
+    row, a single column, 1 x 1, a dense 5 x 5 whose nodes all become hubs),
+    at r = 2n: FP64 equal to the oracle, and both forms equal to LAPACK's
+    pinv (the mixed form to FP32 accuracy)."""
+    m, n = shape
+    rng = np.random.default_rng(m * 10 + n)
+    A = rng.uniform(0.1, 1.0, shape)
+    rowptr = np.arange(0, m * n + 1, n, dtype=np.int64)
+    col = np.tile(np.arange(n, dtype=np.int32), m)
+    val = A.reshape(-1).copy()
+    Y = rng.standard_normal((m, 3))
+    Zp = np.linalg.pinv(A) @ Y
+    h, f, inf = _parity(m, n, rowptr, col, val, Y, 2 * n, 0.3, *chunks)
+    assert (inf["m1"], inf["n1"]) == (f.reo.m1, f.reo.n1)
+    assert min(inf["m1"], inf["n1"]) == 0
+    assert rel(h.apply(torch.from_numpy(Y).to(DEV)).cpu().numpy(), Zp) <= 1e-12
+    g = _handle((m, n, rowptr, col, val)).factor(2 * n, 0.3, "mixed", chunks[0] or BIG, chunks[1] or BIG)
+    assert rel(g.apply(torch.from_numpy(Y).to(DEV)).cpu().numpy(), Zp) <= 1e-5
 
 
 @pytest.mark.parametrize("seed", range(6))
