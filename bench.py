@@ -193,15 +193,29 @@ JACOBI_TRAFFIC_SOURCE = ("ncu dram__bytes.sum.per_second x gpu__time_duration.su
                          "launch (n = 531), profiles/k_jacobi_block_medium.md")
 
 
+def pinv_threshold_report(S, m, n):
+    """Where the singular values sit against the pseudoinverse threshold
+    tau = max(m, n) 2^-52 sigma_1 of Problem 1's Sigma^+ (sigma <= tau counts
+    as zero): how many are at or below tau, and how many lie within 10 tau
+    above it, where the zero / non-zero decision is fragile."""
+    S = np.asarray(S, dtype=np.float64)
+    tau = float(max(m, n) * 2.0 ** -52 * S.max()) if S.size else 0.0
+    return {"tau": tau, "sigma_at_or_below_tau": int(np.count_nonzero(S <= tau)) if S.size else 0,
+            "sigma_within_10x_tau": int(np.count_nonzero((S > tau) & (S <= 10.0 * tau))) if S.size else 0}
+
+
 def factor_accuracy(h):
     """Deviation of the handle's U and V from orthonormal columns (max |entry|
-    of U^T U - I and V^T V - I) and its singular values (host)."""
+    of U^T U - I and V^T V - I), the singular values against the pseudoinverse
+    threshold, and the singular values themselves (host)."""
     import torch
     U, V = h.U(), h.V()
     eye = torch.eye(U.shape[1], dtype=torch.float64, device=U.device)
+    S = np.asarray(h.S())
     out = {"UtU_minus_I_max": float((U.T @ U - eye).abs().max().item()),
            "VtV_minus_I_max": float((V.T @ V - eye).abs().max().item()),
-           "S": np.asarray(h.S())}
+           "pinv_threshold": pinv_threshold_report(S, h.m, h.n),
+           "S": S}
     del U, V
     return out
 

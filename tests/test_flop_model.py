@@ -33,3 +33,16 @@ def test_several_appends_start_from_s_largest_block_triplets():
     F = _bench().flop_model(m=10, n=6, nnz_a21=5, nnz_t=7, m1=4, n1=3, m2=6, n2=3,
                             row_off=np.array([0, 2, 3, 4]), col_off=np.array([0, 1, 2, 3]), r=3, L=2, chunk=2)
     assert F == pytest.approx(6340.0 + 2.0 / 3.0)
+
+
+def test_pinv_threshold_report_hand_example():
+    # m = n = 2^20: tau = 2^20 * 2^-52 * sigma_1 = 2^-32 for sigma_1 = 1
+    b = _bench()
+    tau = 2.0 ** -32
+    S = np.array([1.0, 0.5, 5 * tau, 10 * tau, 10.5 * tau, tau, 0.0])
+    rep = b.pinv_threshold_report(S, 1 << 20, 1 << 20)
+    assert rep["tau"] == tau
+    assert rep["sigma_at_or_below_tau"] == 2          # tau itself and 0
+    assert rep["sigma_within_10x_tau"] == 2           # 5 tau and 10 tau
+    assert b.pinv_threshold_report(np.zeros(0), 3, 4) == {"tau": 0.0, "sigma_at_or_below_tau": 0,
+                                                           "sigma_within_10x_tau": 0}
