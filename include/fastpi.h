@@ -259,8 +259,9 @@ void fastpi_reset_counters(void);
  * engine 0: SIMT FP32 kernel; 1: tcgen05 TF32 kernel with operands rounded
  * to TF32 (one tensor pass); 3: tcgen05 TF32 kernel with split hi + lo
  * operands (three tensor passes, FP32-level accuracy).  The tensor engines
- * return FASTPI_ERR_ARG on devices other than sm_103 (and for M, N or K of
- * 2^31 or more).  Scratch is allocated on the stream; the call returns
+ * return FASTPI_ERR_ARG on devices other than sm_103, for M, N or K of 2^31
+ * or more, for M above 8 388 480 (65 535 tiles of 128 rows), and for M (with
+ * ta) or N (without tb) above 2 097 120 (the operand re-layout's grid).  Scratch is allocated on the stream; the call returns
  * after the stream has finished (it checks the kernels' status word). */
 fastpi_status fastpi_gemm_f32(int ta, int tb, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
                               int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc,

@@ -392,7 +392,7 @@ fastpi_status fastpi_gemm_f32(int ta, int tb, int64_t M, int64_t N, int64_t K, f
       gemm<float>(st, ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
     } else {
       require(M * N == 0 || K == 0 || gemm_tf32_supported(ta != 0, tb != 0, M, N, K, lda, ldb, ldc, A, B, C),
-              FASTPI_ERR_ARG, "the tensor-core GEMM needs an sm_103 device and sizes below 2^31");
+              FASTPI_ERR_ARG, "the tensor-core GEMM needs an sm_103 device and sizes within its grid limits");
       gemm_tf32(st, ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, engine);
     }
     CK(cudaStreamSynchronize(st));

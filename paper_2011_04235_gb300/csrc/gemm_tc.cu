@@ -465,13 +465,16 @@ void launch_tc(cudaStream_t st, int64_t M, int64_t N, int64_t K, float alpha, co
 
 }  // namespace
 
-bool gemm_tf32_supported(bool, bool, int64_t M, int64_t N, int64_t K, int64_t, int64_t, int64_t ldc, const void*,
-                         const void*, const void* C) {
+bool gemm_tf32_supported(bool ta, bool tb, int64_t M, int64_t N, int64_t K, int64_t, int64_t, int64_t ldc,
+                         const void*, const void*, const void* C) {
   // operands that are not K-major or not 16-byte aligned are re-laid into
   // scratch, so only the output and the sizes constrain the tensor path
   if (M <= 0 || N <= 0 || K <= 0) return false;
   if (M >= (int64_t(1) << 31) || N >= (int64_t(1) << 31) || K >= (int64_t(1) << 31)) return false;
   if ((M + TC_BM - 1) / TC_BM > 65535) return false;
+  // the K-major re-layout of a transposed A (M rows) or a non-transposed B
+  // (N rows) runs 32 rows per grid row (gridDim.y <= 65535)
+  if ((ta && (M + 31) / 32 > 65535) || (!tb && (N + 31) / 32 > 65535)) return false;
   (void)ldc;
   (void)C;
   return tc_device_ok();
