@@ -1,11 +1,16 @@
 """Build libfastpi.so in-tree with nvcc for sm_103a (GB300).
 
-Usage: python -m paper_2011_04235_gb300.build [--force]
+Usage: python -m paper_2011_04235_gb300.build [--force] [--phase-clocks]
 
 Each translation unit under csrc/ is compiled in parallel to an object under
 _build/, then linked into paper_2011_04235_gb300/libfastpi.so (CUDA runtime
 linked statically).  An object is rebuilt only when its source or a header
-changed.
+changed, or when the compile flags differ from those of the last build.
+
+--phase-clocks builds the instrumented core SVD: the block Jacobi kernel
+accumulates clock64() per phase of a round (wait, load, Gram, solve, update)
+in one CTA and prints the per-round averages to stderr after each launch.  It
+is a measurement build only; build again without the flag afterwards.
 """
 from __future__ import annotations
 
@@ -38,9 +43,18 @@ def _headers_mtime() -> float:
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, phase_clocks: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
+    flags = FLAGS + (["-DFASTPI_PHASE_CLOCKS"] if phase_clocks else [])
+    stamp = os.path.join(BUILD, "flags.txt")
+    sig = " ".join(ARCH + flags)
+    try:
+        with open(stamp) as fh:
+            if fh.read() != sig:
+                force = True
+    except OSError:
+        force = True
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr_t = _headers_mtime()
     jobs = []
@@ -51,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(so):
         s, o = so
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", s, "-o", o]
+        cmd = [nvcc, *ARCH, *flags, "-c", s, "-o", o]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {os.path.basename(s)}:\n{r.stdout}\n{r.stderr}")
@@ -70,8 +84,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, LIB)
+    with open(stamp, "w") as fh:
+        fh.write(sig)
     return LIB
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, phase_clocks="--phase-clocks" in sys.argv))
