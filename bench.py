@@ -262,6 +262,8 @@ def main():
         w = workloads.make(WORKLOAD)
         vals, secs = [], []
         desc, threads = "", 1
+        for _ in range(args.warmup):        # untimed, as for the GPU arm
+            oracle_sample(w, budget_s=20.0)
         for _ in range(args.steps):
             g, s, desc, threads, _, _ = oracle_sample(w, budget_s=20.0)
             vals.append(g)
