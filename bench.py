@@ -380,8 +380,9 @@ def main():
                 c_times.append(tc - t0)
         h2d = w["rowptr"].nbytes + w["col"].nbytes + w["val"].nbytes + w["Y"].nbytes
         d2h = Zh.nbytes
-        e2e = {"value": world * F / statistics.mean(e_times) / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "seconds_per_step": statistics.mean(e_times),
+        e_value, e_sec = aggregate(world, F, statistics.mean(e_times), pg, dev)   # slowest rank's time
+        e2e = {"value": e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "seconds_per_step": e_sec,
                "create_seconds_per_step": statistics.mean(c_times)}
 
     # roofline of the dominant kernel (the FP32 block-Jacobi core SVD, ALU-bound;
@@ -405,7 +406,7 @@ def main():
                 "avg_launch_ms": avg_ms, "launches_per_step": cnt_mixed["jacobi_launches"] / args.steps}
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:   # the host-core baseline: N = 1 only
         g, s, desc, threads, S_o, res_o = oracle_sample(w, budget_s=20.0)
         cpu = {"value": g, "unit": "GFLOP/s", "cores": threads, "kind": "oracle", "sample": desc, "seconds": s}
         for form, res in (("mixed", res_mixed), ("fp64", res64)):
