@@ -1,4 +1,4 @@
-"""The apply (Problem 1) is capture-safe: no host synchronisation and only
+"""The dense apply (Problem 1, fastpi_apply) is capture-safe: no host synchronisation and only
 stream-ordered allocations, so a caller can record it into a CUDA graph once
 and replay it for every new Y of the same shape (the serving path of
 Application 1)."""
