@@ -53,3 +53,12 @@ def test_binding_rejects_bad_dense_arguments():
     meta = torch.empty(4, 3, dtype=torch.float64, device="meta")
     with pytest.raises(ValueError):
         fastpi._dense_dev(meta, 4, "Y")                                          # not CUDA either
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No CPU fallback: without libfastpi.so the binding raises instead of
+    computing anything."""
+    import pytest
+    from paper_2011_04235_gb300 import fastpi
+    with pytest.raises(ImportError):
+        fastpi.load_library(str(tmp_path / "libfastpi.so"))
