@@ -55,10 +55,12 @@ def test_binding_rejects_bad_dense_arguments():
         fastpi._dense_dev(meta, 4, "Y")                                          # not CUDA either
 
 
-def test_missing_library_fails_loudly(tmp_path):
+def test_missing_library_fails_loudly():
     """No CPU fallback: without libfastpi.so the binding raises instead of
     computing anything."""
     import pytest
     from paper_2011_04235_gb300 import fastpi
+    missing = os.path.join(ROOT, "tests", "no_such_dir", "libfastpi.so")
+    assert not os.path.exists(missing)
     with pytest.raises(ImportError):
-        fastpi.load_library(str(tmp_path / "libfastpi.so"))
+        fastpi.load_library(missing)
