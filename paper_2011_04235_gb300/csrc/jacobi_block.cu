@@ -33,6 +33,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 
 #include "jacobi.cuh"
 
@@ -283,8 +284,8 @@ struct BlkArgs {
 
 // VS: the V panel is staged in shared memory next to the K panel (false: the
 // update reads V's rows straight from L2, for cores whose two panels do not
-// fit in one CTA's shared memory).
-template <int P, bool VS>
+// fit in one CTA's shared memory).  RES: the resident-block schedule below.
+template <int P, bool VS, bool RES>
 __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
   constexpr int B = P / 2;         // columns per block
   constexpr int TW = P / 4;        // Gram tile edge (4 x 4 tiles of TW x TW)
@@ -311,25 +312,58 @@ __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
   const int nq = ldk / 4;   // 16-byte chunks per column
 
   int sweep = 0;
+  // Resident mode: the circle method's pairs are kept, but CTAs swap slots in
+  // fixed pairs (0 <-> 1, 2 <-> 3, ...; the last slot stays when their number
+  // is odd) every round.  Slot s holds {r + s, r - s} in round r, so a move to
+  // s - 1 keeps block r + s and a move to s + 1 keeps r - s: every CTA's pair
+  // shares one block with its previous pair, which stays in shared memory,
+  // and only the other block is waited for and loaded.  held0 / held1: the
+  // blocks in the two physical halves of the panels.
+  int held0 = -1, held1 = -1;
+  const bool slot_fixed = (gridDim.x & 1u) && blockIdx.x == gridDim.x - 1;
 #ifdef FASTPI_PHASE_CLOCKS
   long long t_mark = clock64();
 #endif
   for (;;) {
     for (int rr = 0; rr < a.nb - 1; ++rr) {
       const unsigned t = unsigned(sweep) * unsigned(a.nb - 1) + unsigned(rr);
+      const int slot = (RES && !slot_fixed) ? int(blockIdx.x ^ (t & 1u)) : int(blockIdx.x);
       int bi, bj;
-      circle_pair(blockIdx.x, rr, a.nb, bi, bj);
+      circle_pair(slot, rr, a.nb, bi, bj);
+      // physical halves of bi and bj; `need`: the blocks to wait for and load
+      // (bit 0: bi, bit 1: bj)
+      int hi = 0, hj = 1, need = 3;
+      if (RES) {
+        if (bi == held0 || bi == held1) {
+          hi = bi == held0 ? 0 : 1;
+          hj = 1 - hi;
+          need = 2;
+        } else if (bj == held0 || bj == held1) {
+          hj = bj == held0 ? 0 : 1;
+          hi = 1 - hj;
+          need = 1;
+        }
+        held0 = hi == 0 ? bi : bj;
+        held1 = hi == 0 ? bj : bi;
+      }
+      // physical panel column of logical column c (logical order: the columns
+      // of bi, then those of bj, whatever half holds them)
+      auto pcol = [&](int c) { return (c < B ? hi : hj) * B + (c & (B - 1)); };
       if (tid < P) {
         const int g = tid < B ? bi * B + tid : bj * B + (tid - B);
         s_gcol[tid] = g < n ? g : -1;
       }
-      // wait until the previous round on both blocks is complete
+      // wait until the previous round on the blocks to load is complete
       if (tid == 0) {
         int ok = 1;
-        if (b_ld_acquire(a.ver + bi * VER_STRIDE) < t || b_ld_acquire(a.ver + bj * VER_STRIDE) < t) {
+        auto ready = [&] {
+          return (!(need & 1) || b_ld_acquire(a.ver + bi * VER_STRIDE) >= t) &&
+                 (!(need & 2) || b_ld_acquire(a.ver + bj * VER_STRIDE) >= t);
+        };
+        if (!ready()) {
           const unsigned long long t0 = b_gtimer();
           unsigned spins = 0;
-          while (b_ld_acquire(a.ver + bi * VER_STRIDE) < t || b_ld_acquire(a.ver + bj * VER_STRIDE) < t) {
+          while (!ready()) {
             if ((++spins & 63u) == 0 && b_gtimer() - t0 > B_WAIT_NS) {
               atomicOr(a.status, ST_BARRIER_TIMEOUT);
               ok = 0;
@@ -348,8 +382,9 @@ __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
       // 1. panels: X (first group), Y (second group)
       for (int e = tid; e < P * nq; e += BT) {
         const int c = e / nq, r4 = (e - c * nq) * 4;
+        if (!(need & (c < B ? 1 : 2))) continue;
         const int g = s_gcol[c];
-        float* d = Xs + size_t(c) * ldk + r4;
+        float* d = Xs + size_t(pcol(c)) * ldk + r4;
         if (g >= 0)
           cp_async16(d, a.K + size_t(g) * ldk + r4);
         else
@@ -359,8 +394,9 @@ __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
       if (VS) {
         for (int e = tid; e < P * nq; e += BT) {
           const int c = e / nq, r4 = (e - c * nq) * 4;
+          if (!(need & (c < B ? 1 : 2))) continue;
           const int g = s_gcol[c];
-          float* d = Ys + size_t(c) * ldk + r4;
+          float* d = Ys + size_t(pcol(c)) * ldk + r4;
           if (g >= 0)
             cp_async16(d, a.V + size_t(g) * ldk + r4);
           else
@@ -377,8 +413,10 @@ __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
         float acc[TW * TW];
 #pragma unroll
         for (int i = 0; i < TW * TW; ++i) acc[i] = 0.f;
-        const float* xa = Xs + size_t(tp * TW) * ldk;
-        const float* xb = Xs + size_t(tq * TW) * ldk;
+        // a tile of TW logical columns lies inside one block: consecutive
+        // physical columns
+        const float* xa = Xs + size_t(pcol(tp * TW)) * ldk;
+        const float* xb = Xs + size_t(pcol(tq * TW)) * ldk;
 #pragma unroll 2
         for (int r = lane; r < n; r += 32) {
           float u[TW], w[TW];
@@ -428,17 +466,54 @@ __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
         // the row still has to read)
         constexpr int NH = VS ? 2 : 1;
         constexpr int H = P / NH;
-        for (int it = tid; s_pair_rot && it < NH * n; it += BT) {
+        if (VS && RES) {
+          // resident mode: the panels are updated in place as well, so one
+          // item owns whole rows (no other thread reads the row it rewrites)
+          for (int r = tid; s_pair_rot && r < n; r += BT) {
+            float u[P], v[P];
+#pragma unroll
+            for (int j = 0; j < P; ++j) u[j] = v[j] = 0.f;
+#pragma unroll
+            for (int c = 0; c < P; ++c) {
+              const float xc = Xs[size_t(pcol(c)) * ldk + r];
+              const float yc = Ys[size_t(pcol(c)) * ldk + r];
+              const float4* q4 = reinterpret_cast<const float4*>(Qf + c * GS);
+#pragma unroll
+              for (int j4 = 0; j4 < P / 4; ++j4) {
+                const float4 q = q4[j4];
+                u[4 * j4 + 0] = fmaf(xc, q.x, u[4 * j4 + 0]);
+                u[4 * j4 + 1] = fmaf(xc, q.y, u[4 * j4 + 1]);
+                u[4 * j4 + 2] = fmaf(xc, q.z, u[4 * j4 + 2]);
+                u[4 * j4 + 3] = fmaf(xc, q.w, u[4 * j4 + 3]);
+                v[4 * j4 + 0] = fmaf(yc, q.x, v[4 * j4 + 0]);
+                v[4 * j4 + 1] = fmaf(yc, q.y, v[4 * j4 + 1]);
+                v[4 * j4 + 2] = fmaf(yc, q.z, v[4 * j4 + 2]);
+                v[4 * j4 + 3] = fmaf(yc, q.w, v[4 * j4 + 3]);
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+              const int g = s_gcol[j];
+              if (g >= 0) {
+                __stcg(a.K + size_t(g) * ldk + r, u[j]);
+                __stcg(a.V + size_t(g) * ldk + r, v[j]);
+              }
+              Xs[size_t(pcol(j)) * ldk + r] = g >= 0 ? u[j] : 0.f;
+              Ys[size_t(pcol(j)) * ldk + r] = g >= 0 ? v[j] : 0.f;
+            }
+          }
+        }
+        for (int it = tid; !(VS && RES) && s_pair_rot && it < NH * n; it += BT) {
           const int half = it >= n ? 1 : 0, r = it - half * n, j0 = half * H;
           float u[H], v[H];
 #pragma unroll
           for (int j = 0; j < H; ++j) u[j] = v[j] = 0.f;
 #pragma unroll
           for (int c = 0; c < P; ++c) {
-            const float xc = Xs[size_t(c) * ldk + r];
+            const float xc = Xs[size_t(pcol(c)) * ldk + r];
             float yc;
             if (VS) {
-              yc = Ys[size_t(c) * ldk + r];
+              yc = Ys[size_t(pcol(c)) * ldk + r];
             } else {
               const int g = s_gcol[c];
               yc = g >= 0 ? __ldcg(a.V + size_t(g) * ldk + r) : 0.f;
@@ -464,6 +539,9 @@ __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
               __stcg(a.K + size_t(g) * ldk + r, u[j]);
               __stcg(a.V + size_t(g) * ldk + r, v[j]);
             }
+            // resident mode without a staged V (NH = 1: whole rows): keep the
+            // K panel current in place
+            if (!VS && RES) Xs[size_t(pcol(j0 + j)) * ldk + r] = g >= 0 ? u[j] : 0.f;
           }
         }
       }
@@ -547,6 +625,14 @@ __global__ void k_b_pad_out(const float* __restrict__ Kp, const float* __restric
   V[e] = Vp[int64_t(c) * ldk + r];
 }
 
+// FASTPI_JACOBI_RESIDENT=1 selects the resident-block schedule (same pairs,
+// same arithmetic in the same order, so the same results; fewer loads and
+// waits per round).
+bool resident_schedule() {
+  const char* e = std::getenv("FASTPI_JACOBI_RESIDENT");
+  return e && e[0] == '1' && e[1] == 0;
+}
+
 template <int P, bool VS>
 size_t block_smem(int ldk) {
   return ((VS ? 2 : 1) * size_t(P) * ldk + 4 * size_t(P) * P) * sizeof(float);
@@ -564,9 +650,11 @@ bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats,
   int max_smem = 0;
   CK(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, hc->device));
   if (smem > size_t(max_smem)) return false;
-  allow_max_dynamic_smem((const void*)k_jacobi_block<P, VS>);
+  const bool res = resident_schedule();
+  const void* kern = res ? (const void*)k_jacobi_block<P, VS, true> : (const void*)k_jacobi_block<P, VS, false>;
+  allow_max_dynamic_smem(kern);
   int occ = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi_block<P, VS>, BT, smem));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BT, smem));
   const int grid = nb / 2;
   if (occ < 1 || int64_t(occ) * hc->num_sms < grid) return false;
 
@@ -603,7 +691,7 @@ bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats,
   CK(cudaEventCreate(&ev0));
   CK(cudaEventCreate(&ev1));
   CK(cudaEventRecord(ev0, st));
-  CK(cudaLaunchCooperativeKernel((void*)k_jacobi_block<P, VS>, dim3(grid), dim3(BT), args, smem, st));
+  CK(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(BT), args, smem, st));
   CK_LAUNCH();
   CK(cudaEventRecord(ev1, st));
   k_b_pad_out<<<unsigned((int64_t(n) * n + 255) / 256), 256, 0, st>>>(Kp.get(), Vp.get(), n, ldk, K, V);
