@@ -184,13 +184,17 @@ def oracle_sample(w, budget_s: float = 60.0):
 
 
 # ----------------------------------------------------------------------------- main
-# DRAM bytes (read + write) of one k_jacobi_block<16, 1> launch of this
-# workload (the first row-phase core, n = 531) from an ncu capture of the
-# current kernel; set to None whenever the kernel changes until it is captured
-# again.
-JACOBI_TRAFFIC_BYTES = 660.178841e6 * 4.133280e-3
-JACOBI_TRAFFIC_SOURCE = ("ncu dram__bytes.sum.per_second x gpu__time_duration.sum (DRAM read + write) of one "
-                         "launch (n = 531), profiles/k_jacobi_block_medium.md")
+# DRAM bytes (read + write) of one k_jacobi_block launch of this workload
+# (the first row-phase core, n = 531) from an ncu capture of the current
+# kernel; None whenever the kernel source changed after the capture, until it
+# is captured again.  The last capture (2.73 MB, before the resident-schedule
+# template parameter was added; the default instantiation's loads and stores
+# are the same) is reported beside it.
+JACOBI_TRAFFIC_BYTES = None
+JACOBI_TRAFFIC_LAST_CAPTURE = 660.178841e6 * 4.133280e-3
+JACOBI_TRAFFIC_SOURCE = ("null: kernel source changed after the last ncu capture; last capture = ncu "
+                         "dram__bytes.sum.per_second x gpu__time_duration.sum (DRAM read + write) of one launch "
+                         "(n = 531), profiles/k_jacobi_block_medium.md")
 
 
 def pinv_threshold_report(S, m, n):
@@ -401,6 +405,7 @@ def main():
     roofline = {"kernel": "k_jacobi_block (block one-sided Jacobi core SVD, FP32)", "bound": "alu",
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                 "traffic": JACOBI_TRAFFIC_BYTES, "traffic_source": JACOBI_TRAFFIC_SOURCE,
+                "traffic_last_capture": JACOBI_TRAFFIC_LAST_CAPTURE,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (MEASURED_PEAKS.json)",
                 "time_share": share,
                 "avg_launch_ms": avg_ms, "launches_per_step": cnt_mixed["jacobi_launches"] / args.steps}
