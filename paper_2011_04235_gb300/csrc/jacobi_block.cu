@@ -650,7 +650,9 @@ bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats,
   int max_smem = 0;
   CK(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, hc->device));
   if (smem > size_t(max_smem)) return false;
-  const bool res = resident_schedule();
+  // the resident schedule is used with staged panels only (the form it has
+  // been checked on); cores that stream V from L2 keep the default schedule
+  const bool res = VS && resident_schedule();
   const void* kern = res ? (const void*)k_jacobi_block<P, VS, true> : (const void*)k_jacobi_block<P, VS, false>;
   allow_max_dynamic_smem(kern);
   int occ = 0;
