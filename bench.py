@@ -184,17 +184,11 @@ def oracle_sample(w, budget_s: float = 60.0):
 
 
 # ----------------------------------------------------------------------------- main
-# DRAM bytes (read + write) of one k_jacobi_block launch of this workload
-# (the first row-phase core, n = 531) from an ncu capture of the current
-# kernel; None whenever the kernel source changed after the capture, until it
-# is captured again.  The last capture (2.73 MB, before the resident-schedule
-# template parameter was added; the default instantiation's loads and stores
-# are the same) is reported beside it.
+# DRAM bytes (read + write) per launch of the dominant kernel, from an ncu
+# capture of the current kernel on this workload; None whenever the kernel's
+# source changed after the capture, until it is captured again.
 JACOBI_TRAFFIC_BYTES = None
-JACOBI_TRAFFIC_LAST_CAPTURE = 660.178841e6 * 4.133280e-3
-JACOBI_TRAFFIC_SOURCE = ("null: kernel source changed after the last ncu capture; last capture = ncu "
-                         "dram__bytes.sum.per_second x gpu__time_duration.sum (DRAM read + write) of one launch "
-                         "(n = 531), profiles/k_jacobi_block_medium.md")
+JACOBI_TRAFFIC_SOURCE = "null: the kernel changed after the last ncu capture"
 
 
 def pinv_threshold_report(S, m, n):
@@ -251,7 +245,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -389,8 +383,11 @@ def main():
                "d2h_bytes_per_step": int(d2h), "seconds_per_step": e_sec,
                "create_seconds_per_step": statistics.mean(c_times)}
 
-    # roofline of the dominant kernel (the FP32 block-Jacobi core SVD, ALU-bound;
-    # flops counted as for scalar one-sided Jacobi: sweeps x n(n-1)/2 pairs x 18 n)
+    # roofline of the dominant kernel, the FP32 block-Jacobi SVD of the update
+    # cores (ALU-bound): algorithmic flops = 12 n^3 per n x n core (the dense
+    # SVD model 4 p q^2 + 8 q^3 at p = q = n), over the kernel's own CUDA-event
+    # time on the launching stream.  The rotation work it did (sweeps x
+    # n(n-1)/2 pair visits x 18 n) is reported beside it.
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -398,17 +395,26 @@ def main():
         pass
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12        # TFLOP/s: SMs x FP32 lanes x 2 flop x clock
-    jl = max(cnt_mixed["jacobi_launches"], 1)
-    avg_ms = cnt_mixed["jacobi_ms"] / jl
-    achieved = (cnt_mixed["jacobi_flops"] / jl) / (avg_ms / 1000.0) / 1e12 if avg_ms > 0 else 0.0
-    share = cnt_mixed["jacobi_ms"] / 1000.0 / max(sum(t_mixed), 1e-9)
-    roofline = {"kernel": "k_jacobi_block (block one-sided Jacobi core SVD, FP32)", "bound": "alu",
+    core = cnt_mixed["core32"]
+    jl = max(core["launches"], 1)
+    avg_ms = core["ms"] / jl
+    achieved = core["flops"] / (core["ms"] / 1000.0) / 1e12 if core["ms"] > 0 else 0.0
+    achieved_rot = core["flops_rot"] / (core["ms"] / 1000.0) / 1e12 if core["ms"] > 0 else 0.0
+    step_s = max(sum(t_mixed), 1e-9)
+    roofline = {"kernel": "k_jacobi_block (block one-sided Jacobi SVD of the update cores, FP32)", "bound": "alu",
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                 "traffic": JACOBI_TRAFFIC_BYTES, "traffic_source": JACOBI_TRAFFIC_SOURCE,
-                "traffic_last_capture": JACOBI_TRAFFIC_LAST_CAPTURE,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (MEASURED_PEAKS.json)",
-                "time_share": share,
-                "avg_launch_ms": avg_ms, "launches_per_step": cnt_mixed["jacobi_launches"] / args.steps}
+                "work_per_launch": "12 n^3 flops for an n x n core (n = k + c)",
+                "flops_per_step": core["flops"] / args.steps,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz of MEASURED_PEAKS.json "
+                               "(the file has no FP32 figure)",
+                "rotation_flops_achieved": achieved_rot,
+                "time_share": core["ms"] / 1000.0 / step_s,
+                "avg_launch_ms": avg_ms, "launches_per_step": core["launches"] / args.steps}
+    svd_kernels = {kind: {"launches_per_step": cnt_mixed[kind]["launches"] / args.steps,
+                          "ms_per_step": cnt_mixed[kind]["ms"] / args.steps,
+                          "share": cnt_mixed[kind]["ms"] / 1000.0 / step_s}
+                   for kind in ("blocks", "core32")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:   # the host-core baseline: N = 1 only
@@ -441,6 +447,7 @@ def main():
                                                "rank", "row_chunks", "col_chunks", "jacobi_sweeps_max")},
             "accuracy": acc,
             "roofline": roofline,
+            "svd_kernels": svd_kernels,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(cnt_mixed["kernel_launches"]),

@@ -145,6 +145,23 @@ fastpi_status fastpi_apply_csr(fastpi_t h, int64_t L, int64_t nnz_y, const int64
 fastpi_status fastpi_residual(fastpi_t h, const double* Y, int64_t L, int64_t ldy,
                               const double* Z, int64_t ldz, double* out);
 
+/* fastpi_spmm -- out = A X (m x L) for the handle's sparse matrix A: the
+ * scores of Application 1's multi-label regression when X = Z and A holds
+ * held-out instances.  X: device float64 n x L row-major (ldx >= L); out:
+ * device float64 m x L row-major (ldo >= L), overwritten.  The call returns
+ * when out is written.  Errors: FASTPI_ERR_ARG (sizes, null pointers),
+ * FASTPI_ERR_STATE (a handle made from factors has no matrix). */
+fastpi_status fastpi_spmm(fastpi_t h, const double* X, int64_t L, int64_t ldx, double* out, int64_t ldo);
+
+/* fastpi_recon_error -- |A - U Sigma V^T|_F / |A|_F, the reconstruction error
+ * of the low-rank approximation behind the pseudoinverse (Section 4), from the
+ * stored factors, in FP64: |A|^2 - 2 sum_i sigma_i u_i^T A v_i +
+ * sigma^T ((U^T U) o (V^T V)) sigma (exact also when U and V are orthonormal
+ * only to rounding), so an error below about 1e-7 is resolved only to
+ * rounding.  *out: host double.  Errors: FASTPI_ERR_STATE (before
+ * fastpi_factor, or a handle made from factors). */
+fastpi_status fastpi_recon_error(fastpi_t h, double* out);
+
 /*
  * fastpi_residual_noalloc -- |A Z - Y|_F in FP64, like fastpi_residual, but
  * without a handle and without allocating anything.  The paper has no
@@ -158,9 +175,18 @@ fastpi_status fastpi_residual(fastpi_t h, const double* Y, int64_t L, int64_t ld
  *      it must pass the checks fastpi_create makes, else the result is
  *      undefined.
  *   Y: device m x L (ldy), Z: device n x L (ldz), row-major.  *out: host double.
- *   cuda_stream: the stream to run on (NULL = legacy default stream).
+ *   cuda_stream: the stream to run on (NULL = legacy default stream of the
+ *   current device).  The call runs on the stream's device, whatever device
+ *   is current; A, Y and Z must be on that device.  The caller's current
+ *   device is restored on return.
  * FASTPI_ERR_ARG when m > FASTPI_NOALLOC_MAX_ROWS or an argument is invalid.
- * The first call on each device looks up the scratch address on that device.
+ * The first call on each device is its set-up: it looks up the scratch
+ * address on that device and, under CUDA's lazy module loading, loads this
+ * entry point's kernels and the scratch array there, which takes device
+ * memory once.  Make one call on each device (m = 0 is enough) before the
+ * memory budget is locked; later calls allocate nothing.  A cudaDeviceReset
+ * invalidates that set-up like every other resource of the process on the
+ * device: do not call this entry point on a device after resetting it.
  * All calls share the scratch, so calls that overlap on the GPU race; each
  * call overwrites all the scratch it reads.
  * The call synchronises the stream to return the value.
@@ -217,6 +243,23 @@ fastpi_status fastpi_truncate(fastpi_t h, int64_t r);
  * the same k.  Errors: FASTPI_ERR_ARG (k outside (0, 1)), FASTPI_ERR_CUDA. */
 fastpi_status fastpi_reorder(fastpi_t h, double k);
 
+/* Eq. 1 (Section 3.3) alone: Algorithm 2 with hub ratio k, then the SVD of
+ * every diagonal block A11^(i) of A11, keeping its s_i = min(ceil(alpha n_1i),
+ * m_1i, n_1i) largest singular values, alpha = r / n -- the first stage of
+ * fastpi_factor with the same r, k and precision, stopped there.
+ *   sigma: host float64[cap]; receives the S = sum of s_i kept values, block by
+ *          block in the block order of fastpi_get_blocks, descending within a
+ *          block (ties: lower column of the block's Jacobi result first).
+ *   S_out: host int64, receives S (also when cap is too small).
+ * Afterwards fastpi_get_perm, fastpi_get_blocks and fastpi_get_info (the
+ * reordering fields and S) are valid; the factor getters return
+ * FASTPI_ERR_STATE.  Errors: FASTPI_ERR_ARG (r < 1, k outside (0, 1), unknown
+ * precision, S_out NULL, or cap < S: the values are then not written),
+ * FASTPI_ERR_STATE (a handle made from factors), FASTPI_ERR_CUDA,
+ * FASTPI_ERR_NO_CONVERGENCE. */
+fastpi_status fastpi_block_svd(fastpi_t h, int64_t r, double k, fastpi_precision prec, double* sigma,
+                               int64_t cap, int64_t* S_out);
+
 /* Getters (valid after fastpi_factor; FASTPI_ERR_STATE before; fastpi_get_perm,
  * fastpi_get_blocks and fastpi_get_info also after fastpi_reorder). */
 fastpi_status fastpi_get_rank(fastpi_t h, int64_t* r_out);            /* host int64 */
@@ -238,15 +281,21 @@ fastpi_status fastpi_get_info(fastpi_t h, fastpi_info* info);          /* host s
 
 /* Process-wide diagnostic counters (no citation: instrumentation of this
  * library, not a step of the method).  kernel_launches counts every kernel
- * this library launched; the jacobi_* fields cover the batched Jacobi SVD
- * kernel: launches, summed device time from CUDA events recorded on the
- * launching stream, and algorithmic flops, counted per problem as
- * sweeps * q(q-1)/2 pair visits * (12 p + 6 q) for a p x q problem. */
+ * this library launched.  The svd_* arrays cover the SVD launches, indexed
+ * [0] batched Jacobi of the A11 blocks (Eq. 1), [1] FP32 block-Jacobi SVD of
+ * an update core (Eqs. 2 / 3, mixed form), [2] FP64 SVD of an update core
+ * (FP64 form): launches; summed device time from CUDA events recorded on the
+ * launching stream; the dense-SVD flop model 4 p q^2 + 8 q^3 per p x q problem
+ * (12 n^3 for an n x n core); and the rotation work done, sweeps x q(q-1)/2
+ * pair visits x (12 p + 6 q).  core_resident_launches: core SVD launches that
+ * used the resident-block schedule. */
 typedef struct {
   uint64_t kernel_launches;
-  uint64_t jacobi_launches;
-  double jacobi_ms;
-  double jacobi_flops;
+  uint64_t svd_launches[3];
+  double svd_ms[3];
+  double svd_flops[3];
+  double svd_flops_rot[3];
+  uint64_t core_resident_launches;
 } fastpi_counters;
 fastpi_status fastpi_get_counters(fastpi_counters* out);   /* host struct */
 void fastpi_reset_counters(void);

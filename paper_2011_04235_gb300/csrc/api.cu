@@ -228,6 +228,27 @@ fastpi_status fastpi_reorder(fastpi_t h, double k) {
   API_END(h)
 }
 
+fastpi_status fastpi_block_svd(fastpi_t h, int64_t r, double k, fastpi_precision prec, double* sigma, int64_t cap,
+                               int64_t* S_out) {
+  if (!h) return FASTPI_ERR_ARG;
+  API_BEGIN
+  use_device(h);
+  require(r >= 1, FASTPI_ERR_ARG, "target rank r must be >= 1");
+  require(k > 0.0 && k < 1.0 && std::isfinite(k), FASTPI_ERR_ARG, "hub ratio k must lie in (0, 1)");
+  require(prec == FASTPI_FP64 || prec == FASTPI_MIXED_TF32, FASTPI_ERR_ARG, "unknown precision");
+  require(S_out != nullptr && cap >= 0 && (cap == 0 || sigma != nullptr), FASTPI_ERR_ARG,
+          "need S_out, and sigma when cap > 0");
+  require(h->has_matrix, FASTPI_ERR_STATE, "handle made from factors has no matrix");
+  h->factored = false;
+  h->reordered = false;
+  std::vector<double> sig;
+  fastpi::block_svd_only(h, r, k, prec, sig);
+  *S_out = int64_t(sig.size());
+  require(int64_t(sig.size()) <= cap, FASTPI_ERR_ARG, "sigma holds fewer than S values (S returned in S_out)");
+  if (!sig.empty()) std::memcpy(sigma, sig.data(), sig.size() * sizeof(double));
+  API_END(h)
+}
+
 fastpi_status fastpi_apply(fastpi_t h, const double* Y, int64_t L, int64_t ldy, double* Z, int64_t ldz) {
   if (!h) return FASTPI_ERR_ARG;
   API_BEGIN
@@ -282,6 +303,29 @@ fastpi_status fastpi_residual(fastpi_t h, const double* Y, int64_t L, int64_t ld
   require(L == 0 || (Y && Z), FASTPI_ERR_ARG, "null Y or Z");
   require(h->has_matrix, FASTPI_ERR_STATE, "handle made from factors has no matrix");
   *out = residual(h, Y, L, ldy, Z, ldz);
+  API_END(h)
+}
+
+fastpi_status fastpi_spmm(fastpi_t h, const double* X, int64_t L, int64_t ldx, double* out, int64_t ldo) {
+  if (!h) return FASTPI_ERR_ARG;
+  API_BEGIN
+  use_device(h);
+  require(L >= 0 && ldx >= L && ldo >= L, FASTPI_ERR_ARG, "need L >= 0, ldx >= L, ldo >= L");
+  require(L == 0 || (X && out), FASTPI_ERR_ARG, "null X or out");
+  require(h->has_matrix, FASTPI_ERR_STATE, "handle made from factors has no matrix");
+  spmm(h, X, L, ldx, out, ldo);
+  CK(cudaStreamSynchronize(h->stream));
+  API_END(h)
+}
+
+fastpi_status fastpi_recon_error(fastpi_t h, double* out) {
+  if (!h) return FASTPI_ERR_ARG;
+  API_BEGIN
+  use_device(h);
+  require(out != nullptr, FASTPI_ERR_ARG, "out is NULL");
+  require_factored(h);
+  require(h->has_matrix, FASTPI_ERR_STATE, "handle made from factors has no matrix");
+  *out = recon_error(h);
   API_END(h)
 }
 

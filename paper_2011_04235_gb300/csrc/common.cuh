@@ -24,8 +24,12 @@ void check_cuda(cudaError_t e, const char* what, const char* file, int line);
 void note_launch(const char* file, int line);
 #define CK(x) ::fastpi::check_cuda((x), #x, __FILE__, __LINE__)
 #define CK_LAUNCH() ::fastpi::note_launch(__FILE__, __LINE__)
-// Adds one event-timed launch of the Jacobi kernel to the process counters.
-void note_jacobi(double ms, double flops);
+// Adds one event-timed SVD launch to the process counters: kind SVD_BLOCKS
+// (batched Jacobi of the A11 blocks, Eq. 1), SVD_CORE32 (FP32 block-Jacobi
+// core SVD) or SVD_CORE64 (FP64 core SVD); flops_model = 4 p q^2 + 8 q^3 per
+// p x q problem, flops_rot = sweeps x q (q - 1) / 2 x (12 p + 6 q).
+enum { SVD_BLOCKS = 0, SVD_CORE32 = 1, SVD_CORE64 = 2 };
+void note_svd(int kind, double ms, double flops_model, double flops_rot, bool resident = false);
 void read_counters(fastpi_counters* out);
 void reset_counters();
 

@@ -802,7 +802,7 @@ struct Phase {
     if (!done) {
       std::vector<JacobiProblem<T>> pr(1);
       pr[0] = JacobiProblem<T>{K.get(), J.get(), n, n, int(n), int(n)};
-      js = jacobi_svd_batched<T>(h, pr, jsig.get(), jperm.get());
+      js = jacobi_svd_batched<T>(h, pr, jsig.get(), jperm.get(), sizeof(T) == 8 ? SVD_CORE64 : SVD_CORE32);
     }
     sweeps_max = std::max(sweeps_max, js.max_sweeps_used);
     int32_t rks[2];
@@ -912,29 +912,30 @@ struct Timer {
 template <typename T>
 using BlockSvdFn = std::function<JacobiStats(const std::vector<JacobiProblem<T>>&, double*&, int32_t*&)>;
 
+// Eq. 1 for the blocks of A11: dense copies in the working precision, one
+// batched Jacobi SVD over all blocks, and the kept singular values on the host
+// (sig_all[g] for block triplet g: blocks in order, descending within a block).
 template <typename T>
-void factor_impl(fastpi_ctx* h, Factors& F, int64_t r, double kratio, int64_t chunk_row, int64_t chunk_col,
-                 const BlockSvdFn<T>& block_svd) {
-  cudaStream_t st = h->stream;
-  const int64_t m = h->m, n = h->n;
-  fastpi_info& info = h->info;
-  Timer tm(st);
-  // ---- Algorithm 2 + split
-  tm.start();
-  Reordering& R = F.R;
-  run_reorder(h, kratio, R);
-  SparseCols A21, Tc;
-  split_border(h, R, A21, Tc);
-  A11Blocks blk;
-  extract_blocks(h, R, r, blk);
-  info.ms_reorder = tm.stop();
-  const int64_t m1 = R.m1, n1 = R.n1, m2 = m - m1, n2 = n - n1, S = blk.S;
+struct BlockStage {
+  std::vector<BlkDesc> bd;
+  DArr<T> bdata, vbuf;
+  DArr<double> bsig_own;
+  DArr<int32_t> bperm_own;
+  double* bsig = nullptr;
+  int32_t* bperm = nullptr;
+  int64_t utot = 0, vtot = 0, sigtot = 0;
+  JacobiStats js;
+  std::vector<double> sig_all;
+};
 
-  // ---- Eq. 1: batched SVD of the A11 blocks
-  tm.start();
-  std::vector<BlkDesc> bd(blk.B);
+template <typename T>
+void run_block_stage(fastpi_ctx* h, const Reordering& R, const A11Blocks& blk, const BlockSvdFn<T>& block_svd,
+                     BlockStage<T>& out) {
+  cudaStream_t st = h->stream;
+  const int64_t S = blk.S;
+  std::vector<BlkDesc>& bd = out.bd;
+  bd.resize(blk.B);
   std::vector<JacobiProblem<T>> probs;
-  std::vector<int64_t> prob_of;
   int64_t vtot = 0, utot = 0, sigtot = 0;
   for (int64_t b = 0; b < blk.B; ++b) {
     BlkDesc& d = bd[b];
@@ -957,12 +958,13 @@ void factor_impl(fastpi_ctx* h, Factors& F, int64_t r, double kratio, int64_t ch
       d.v_off = d.sig_off = 0;
     }
   }
-  DArr<T> bdata(std::max<int64_t>(blk.total, 1), st), vbuf(std::max<int64_t>(vtot, 1), st);
+  out.bdata = DArr<T>(std::max<int64_t>(blk.total, 1), st);
+  out.vbuf = DArr<T>(std::max<int64_t>(vtot, 1), st);
   if (blk.total > 0) {
     if (sizeof(T) == 8)
-      CK(cudaMemcpyAsync(bdata.get(), blk.data.get(), size_t(blk.total) * 8, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(out.bdata.get(), blk.data.get(), size_t(blk.total) * 8, cudaMemcpyDeviceToDevice, st));
     else {
-      k_convert<T, double><<<g1(blk.total), 256, 0, st>>>(blk.total, blk.data.get(), bdata.get());
+      k_convert<T, double><<<g1(blk.total), 256, 0, st>>>(blk.total, blk.data.get(), out.bdata.get());
       CK_LAUNCH();
     }
   }
@@ -970,13 +972,51 @@ void factor_impl(fastpi_ctx* h, Factors& F, int64_t r, double kratio, int64_t ch
     const BlkDesc& d = bd[b];
     if (d.s_b == 0) continue;
     int64_t p = std::max(d.m_b, d.n_b), q = std::min(d.m_b, d.n_b);
-    probs.push_back(JacobiProblem<T>{bdata.get() + d.data_off, vbuf.get() + d.v_off, p, q, int(p), int(q)});
+    probs.push_back(
+        JacobiProblem<T>{out.bdata.get() + d.data_off, out.vbuf.get() + d.v_off, p, q, int(p), int(q)});
   }
-  DArr<double> bsig_own(std::max<int64_t>(sigtot, 1), st);
-  DArr<int32_t> bperm_own(std::max<int64_t>(sigtot, 1), st);
-  double* bsig = bsig_own.get();
-  int32_t* bperm = bperm_own.get();
-  JacobiStats bjs = block_svd(probs, bsig, bperm);
+  out.bsig_own = DArr<double>(std::max<int64_t>(sigtot, 1), st);
+  out.bperm_own = DArr<int32_t>(std::max<int64_t>(sigtot, 1), st);
+  out.bsig = out.bsig_own.get();
+  out.bperm = out.bperm_own.get();
+  out.js = block_svd(probs, out.bsig, out.bperm);
+  out.utot = utot;
+  out.vtot = vtot;
+  out.sigtot = sigtot;
+  std::vector<double> hsig(std::max<int64_t>(sigtot, 1));
+  out.sig_all.assign(std::max<int64_t>(S, 1), 0.0);
+  if (sigtot > 0) d2h_sync(hsig.data(), out.bsig, size_t(sigtot) * 8, st);
+  for (const BlkDesc& d : bd)
+    for (int64_t t = 0; t < d.s_b; ++t) out.sig_all[d.soff + t] = hsig[d.sig_off + t];
+}
+
+template <typename T>
+void factor_impl(fastpi_ctx* h, Factors& F, int64_t r, double kratio, int64_t chunk_row, int64_t chunk_col,
+                 const BlockSvdFn<T>& block_svd) {
+  cudaStream_t st = h->stream;
+  const int64_t m = h->m, n = h->n;
+  fastpi_info& info = h->info;
+  Timer tm(st);
+  // ---- Algorithm 2 + split
+  tm.start();
+  Reordering& R = F.R;
+  run_reorder(h, kratio, R);
+  SparseCols A21, Tc;
+  split_border(h, R, A21, Tc);
+  A11Blocks blk;
+  extract_blocks(h, R, r, blk);
+  info.ms_reorder = tm.stop();
+  const int64_t m1 = R.m1, n1 = R.n1, m2 = m - m1, n2 = n - n1, S = blk.S;
+
+  // ---- Eq. 1: batched SVD of the A11 blocks
+  tm.start();
+  BlockStage<T> bs;
+  run_block_stage<T>(h, R, blk, block_svd, bs);
+  std::vector<BlkDesc>& bd = bs.bd;
+  double* bsig = bs.bsig;
+  int32_t* bperm = bs.bperm;
+  const int64_t utot = bs.utot;
+  JacobiStats bjs = bs.js;
   // Row phase basis: V1 (n1 x k0); U1 packed per block (all S); Sigma1
   const int64_t s_row = std::min<int64_t>({(r * n1 + n - 1) / n, S + m2, n1});
   const int64_t cr = chunk_row > 0 ? chunk_row : DEFAULT_CHUNK;
@@ -988,10 +1028,7 @@ void factor_impl(fastpi_ctx* h, Factors& F, int64_t r, double kratio, int64_t ch
   std::vector<int32_t> pos(std::max<int64_t>(S, 1));
   int64_t k0 = S;
   {
-    std::vector<double> hsig(std::max<int64_t>(sigtot, 1)), sig_all(std::max<int64_t>(S, 1));
-    if (sigtot > 0) d2h_sync(hsig.data(), bsig, size_t(sigtot) * 8, st);
-    for (const BlkDesc& d : bd)
-      for (int64_t t = 0; t < d.s_b; ++t) sig_all[d.soff + t] = hsig[d.sig_off + t];
+    const std::vector<double>& sig_all = bs.sig_all;
     for (int64_t g = 0; g < S; ++g) pos[g] = int32_t(g);
     if (cr < m2 && S > s_row) {
       std::vector<int32_t> idx(S);
@@ -1018,7 +1055,7 @@ void factor_impl(fastpi_ctx* h, Factors& F, int64_t r, double kratio, int64_t ch
       if (d.s_b > 0) act.push_back(d);
     DArr<BlkDesc> d_act(int64_t(act.size()), st);
     CK(cudaMemcpyAsync(d_act.get(), act.data(), sizeof(BlkDesc) * act.size(), cudaMemcpyHostToDevice, st));
-    k_block_out<T><<<unsigned(act.size()), 128, 0, st>>>(d_act.get(), bdata.get(), vbuf.get(), bsig,
+    k_block_out<T><<<unsigned(act.size()), 128, 0, st>>>(d_act.get(), bs.bdata.get(), bs.vbuf.get(), bsig,
                                                          bperm, d_pos.get(), kmax_r, rowp.U(), U1.get(),
                                                          rowp.S());
     CK_LAUNCH();
@@ -1199,6 +1236,91 @@ __global__ void k_sum(const double* x, int64_t n, double* out) {
     double t = 0;
     for (int w = 0; w < int(blockDim.x >> 5); ++w) t += ws[w];
     *out = t;
+  }
+}
+
+// out (m x L, ld ldo) = A X for A in CSR and X (n x L, ld ldx), FP64.  One
+// warp per row; lane l owns the columns l, l + 32, ... of a pass of RES_RP * 32
+// columns, so each nonzero of the row is read once per pass.
+__global__ void k_spmm_rows(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            const double* __restrict__ val, int64_t m, int64_t L, const double* __restrict__ X,
+                            int64_t ldx, double* __restrict__ out, int64_t ldo) {
+  const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= m) return;
+  const int64_t e0 = rowptr[i], e1 = rowptr[i + 1];
+  for (int64_t l0 = 0; l0 < L; l0 += 32 * RES_RP) {
+    double s[RES_RP];
+#pragma unroll
+    for (int u = 0; u < RES_RP; ++u) s[u] = 0.0;
+    for (int64_t e = e0; e < e1; ++e) {
+      const double v = val[e];
+      const double* xr = X + int64_t(col[e]) * ldx;
+#pragma unroll
+      for (int u = 0; u < RES_RP; ++u) {
+        const int64_t l = l0 + lane + 32 * u;
+        if (l < L) s[u] = fma(v, xr[l], s[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < RES_RP; ++u) {
+      const int64_t l = l0 + lane + 32 * u;
+      if (l < L) out[i * ldo + l] = s[u];
+    }
+  }
+}
+
+// cross[j] = sum_i U[i, j] AV[i, j] (one CTA per column j, fixed order).
+__global__ void k_col_dots(int64_t m, int64_t r, const double* __restrict__ U, const double* __restrict__ AV,
+                           double* cross) {
+  __shared__ double ws[32];
+  const int64_t j = blockIdx.x;
+  double s = 0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) s = fma(U[i * r + j], AV[i * r + j], s);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += ws[w];
+    cross[j] = t;
+  }
+}
+
+// out[0] = |A|_F^2 - 2 sum_j s_j cross_j + sum_{i,j} s_i s_j Gu_ij Gv_ij, one CTA.
+__global__ void k_recon_total(int64_t nnz, const double* __restrict__ val, int64_t r, const double* __restrict__ S,
+                              const double* __restrict__ cross, const double* __restrict__ Gu,
+                              const double* __restrict__ Gv, double* out) {
+  __shared__ double ws[3][32];
+  double a2 = 0, cr = 0, q = 0;
+  for (int64_t e = threadIdx.x; e < nnz; e += blockDim.x) a2 = fma(val[e], val[e], a2);
+  for (int64_t j = threadIdx.x; j < r; j += blockDim.x) cr = fma(S[j], cross[j], cr);
+  for (int64_t e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int64_t i = e / r, j = e % r;
+    q = fma(S[i] * S[j], Gu[e] * Gv[e], q);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    cr += __shfl_xor_sync(0xffffffffu, cr, o);
+    q += __shfl_xor_sync(0xffffffffu, q, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    ws[0][threadIdx.x >> 5] = a2;
+    ws[1][threadIdx.x >> 5] = cr;
+    ws[2][threadIdx.x >> 5] = q;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t0 = 0, t1 = 0, t2 = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+      t0 += ws[0][w];
+      t1 += ws[1][w];
+      t2 += ws[2][w];
+    }
+    out[0] = t0;
+    out[1] = t0 - 2.0 * t1 + t2;
   }
 }
 
@@ -1529,6 +1651,55 @@ void truncate_factors(fastpi_ctx* h, int64_t r) {
   CK(cudaStreamSynchronize(st));
 }
 
+// Algorithm 2 and Eq. 1 only: the kept singular values of every A11 block.
+template <typename T>
+void block_stage_only(fastpi_ctx* h, int64_t r, double kratio, std::vector<double>& sig_out) {
+  Factors* F = new Factors();
+  h->info = fastpi_info{};
+  h->factored = false;
+  h->reordered = false;
+  int64_t S = 0;
+  try {
+    Timer tm(h->stream);
+    tm.start();
+    run_reorder(h, kratio, F->R);
+    A11Blocks blk;
+    extract_blocks(h, F->R, r, blk);
+    h->info.ms_reorder = tm.stop();
+    tm.start();
+    BlockStage<T> bs;
+    run_block_stage<T>(h, F->R, blk, own_block_svd<T>(h), bs);
+    h->info.ms_block_svd = tm.stop();
+    S = blk.S;
+    sig_out.assign(bs.sig_all.begin(), bs.sig_all.begin() + S);
+    h->info.jacobi_sweeps_max = bs.js.max_sweeps_used;
+  } catch (...) {
+    delete F;
+    throw;
+  }
+  const Reordering& R = F->R;
+  h->info.m = h->m;
+  h->info.n = h->n;
+  h->info.nnz = h->nnz;
+  h->info.m1 = R.m1;
+  h->info.n1 = R.n1;
+  h->info.m2 = h->m - R.m1;
+  h->info.n2 = h->n - R.n1;
+  h->info.num_blocks = R.num_blocks;
+  h->info.iterations = R.iterations;
+  h->info.S = S;
+  delete h->fac;
+  h->fac = F;
+  h->reordered = true;
+}
+
+void block_svd_only(fastpi_ctx* h, int64_t r, double k, fastpi_precision prec, std::vector<double>& sig) {
+  if (prec == FASTPI_FP64)
+    block_stage_only<double>(h, r, k, sig);
+  else
+    block_stage_only<float>(h, r, k, sig);
+}
+
 void reorder_only(fastpi_ctx* h, double k) {
   Factors* F = new Factors();
   h->info = fastpi_info{};
@@ -1640,6 +1811,45 @@ void apply_csr(fastpi_ctx* h, int64_t L, int64_t nnz_y, const int64_t* yrowptr, 
     gemm_f32(st, false, true, n, L, r, 1.f, F.V32.get(), ldr, WtT.get(), ldr, 0.f, Zf.get(), L);
     copy2d<double, float>(st, n, L, Zf.get(), L, Z, ldz);
   }
+}
+
+void spmm(fastpi_ctx* h, const double* X, int64_t L, int64_t ldx, double* out, int64_t ldo) {
+  cudaStream_t st = h->stream;
+  if (h->m <= 0 || L <= 0) return;
+  k_spmm_rows<<<g1(h->m * 32), 256, 0, st>>>(h->rowptr, h->col, h->val, h->m, L, X, ldx, out, ldo);
+  CK_LAUNCH();
+}
+
+double recon_error(fastpi_ctx* h) {
+  Factors& F = *h->fac;
+  cudaStream_t st = h->stream;
+  const int64_t m = F.m, n = F.n, r = F.rank;
+  const int64_t ldr = std::max<int64_t>(r, 1);
+  DArr<double> Ud, Vd;
+  const double* U = F.U64.get();
+  const double* V = F.V64.get();
+  if (F.prec != FASTPI_FP64) {
+    Ud = DArr<double>(m * ldr, st);
+    Vd = DArr<double>(n * ldr, st);
+    copy2d<double, float>(st, m, r, F.U32.get(), ldr, Ud.get(), ldr);
+    copy2d<double, float>(st, n, r, F.V32.get(), ldr, Vd.get(), ldr);
+    U = Ud.get();
+    V = Vd.get();
+  }
+  DArr<double> AV(m * ldr, st), cross(ldr, st), Gu(ldr * ldr, st), Gv(ldr * ldr, st), tot(2, st);
+  if (r > 0) {
+    spmm(h, V, r, ldr, AV.get(), ldr);
+    k_col_dots<<<unsigned(r), 256, 0, st>>>(m, r, U, AV.get(), cross.get());
+    CK_LAUNCH();
+    gemm<double>(st, true, false, r, r, m, 1.0, U, ldr, U, ldr, 0.0, Gu.get(), ldr);
+    gemm<double>(st, true, false, r, r, n, 1.0, V, ldr, V, ldr, 0.0, Gv.get(), ldr);
+  }
+  k_recon_total<<<1, 1024, 0, st>>>(h->nnz, h->val, r, F.S_d.get(), cross.get(), Gu.get(), Gv.get(), tot.get());
+  CK_LAUNCH();
+  double t[2] = {0, 0};
+  d2h_sync(t, tot.get(), sizeof t, st);
+  if (!(t[0] > 0)) return 0.0;
+  return std::sqrt(std::max(t[1], 0.0) / t[0]);
 }
 
 double residual(fastpi_ctx* h, const double* Y, int64_t L, int64_t ldy, const double* Z, int64_t ldz) {

@@ -34,11 +34,19 @@ void load_factors(fastpi_ctx* h, int64_t r, const double* S, const double* U, in
                   int64_t ldv, fastpi_precision prec, bool on_device);
 // Keep the r largest triplets of the current factors.
 void truncate_factors(fastpi_ctx* h, int64_t r);
+// Algorithm 2 and Eq. 1 alone: the kept singular values of the A11 blocks
+// (block order, descending within a block); the reordering is kept for the
+// permutation / block getters.
+void block_svd_only(fastpi_ctx* h, int64_t r, double k, fastpi_precision prec, std::vector<double>& sig);
 // Algorithm 2 alone: the reordering is kept for the permutation / block getters.
 void reorder_only(fastpi_ctx* h, double k);
 void apply_dense(fastpi_ctx* h, const double* Y, int64_t L, int64_t ldy, double* Z, int64_t ldz);
 void apply_csr(fastpi_ctx* h, int64_t L, int64_t nnz_y, const int64_t* yrowptr, const int32_t* ycol,
                const double* yval, double* Z, int64_t ldz);
 double residual(fastpi_ctx* h, const double* Y, int64_t L, int64_t ldy, const double* Z, int64_t ldz);
+// out (m x L) = A X (X: n x L), FP64, device buffers.
+void spmm(fastpi_ctx* h, const double* X, int64_t L, int64_t ldx, double* out, int64_t ldo);
+// |A - U diag(S) V^T|_F / |A|_F from the stored factors.
+double recon_error(fastpi_ctx* h);
 
 }  // namespace fastpi

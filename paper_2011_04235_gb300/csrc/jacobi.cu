@@ -375,7 +375,7 @@ template <> struct Eps<float> { static constexpr double v = 1.1920928955078125e-
 // outputs at sig / perm + out_off[b].
 template <typename T>
 JacobiStats run_bucket(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& probs,
-                       const std::vector<int64_t>& out_off, double* sig, int32_t* perm) {
+                       const std::vector<int64_t>& out_off, double* sig, int32_t* perm, int kind) {
   JacobiStats stats;
   const int nprob = int(probs.size());
   if (nprob == 0) return stats;
@@ -504,12 +504,13 @@ JacobiStats run_bucket(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& probs
     CK(cudaEventElapsedTime(&ms, ev0, ev1));
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
-    double flops = 0;
+    double flops = 0, model = 0;
     for (int b = 0; b < nprob; ++b) {
       const double p = dp[b].p, q = dp[b].q;
       flops += double(hs[b].sweeps) * (q * (q - 1) / 2) * (12 * p + 6 * q);
+      model += 4 * p * q * q + 8 * q * q * q;
     }
-    note_jacobi(ms, flops);
+    note_svd(kind, ms, model, flops);
   }
   if (stat & ST_BARRIER_TIMEOUT) fail(FASTPI_ERR_NO_CONVERGENCE, "Jacobi SVD: device-wide barrier timed out");
   stats.hit_cap = (stat & ST_JACOBI_SWEEPS) != 0;
@@ -538,7 +539,7 @@ int tile_class(const JacobiProblem<T>& P) {
 // of the largest one, and its convergence threshold).
 template <typename T>
 JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& probs, double* sig,
-                               int32_t* perm) {
+                               int32_t* perm, int kind) {
   JacobiStats stats;
   const int nprob = int(probs.size());
   if (nprob == 0) return stats;
@@ -554,7 +555,7 @@ JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>
   }
   for (int c = 0; c < NCLASS; ++c) {
     if (bucket[c].empty()) continue;
-    const JacobiStats js = run_bucket<T>(h, bucket[c], off[c], sig, perm);
+    const JacobiStats js = run_bucket<T>(h, bucket[c], off[c], sig, perm, kind);
     stats.max_sweeps_used = std::max(stats.max_sweeps_used, js.max_sweeps_used);
     stats.hit_cap = stats.hit_cap || js.hit_cap;
   }
@@ -594,8 +595,8 @@ template void jacobi_sort_columns<double>(fastpi_ctx*, const std::vector<JacobiP
 template void jacobi_sort_columns<float>(fastpi_ctx*, const std::vector<JacobiProblem<float>>&, double*, int32_t*);
 
 template JacobiStats jacobi_svd_batched<double>(fastpi_ctx*, const std::vector<JacobiProblem<double>>&, double*,
-                                                int32_t*);
+                                                int32_t*, int);
 template JacobiStats jacobi_svd_batched<float>(fastpi_ctx*, const std::vector<JacobiProblem<float>>&, double*,
-                                               int32_t*);
+                                               int32_t*, int);
 
 }  // namespace fastpi

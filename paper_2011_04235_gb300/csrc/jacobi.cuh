@@ -27,7 +27,7 @@ struct JacobiStats {
 // to perm[...], where sig_off_b = sum of q over earlier problems.
 template <typename T>
 JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& probs, double* sig,
-                               int32_t* perm);
+                               int32_t* perm, int kind = SVD_BLOCKS);
 
 // Only the last step of jacobi_svd_batched: column norms of each (already
 // orthogonalised) A and the descending sort, into sig / perm.

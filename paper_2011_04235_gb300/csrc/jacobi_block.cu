@@ -639,7 +639,8 @@ size_t block_smem(int ldk) {
 }
 
 template <int P, bool VS>
-bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats, float* ms_out, int* sweeps) {
+bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats, float* ms_out, int* sweeps,
+                  bool* used_res) {
   cudaStream_t st = hc->stream;
   constexpr int B = P / 2;
   int nb = (n + B - 1) / B;
@@ -723,6 +724,7 @@ bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats,
 #endif
   *ms_out = ms;
   *sweeps = ho[0];
+  *used_res = res;
   if (stats) {
     stats->max_sweeps_used = ho[0];
     stats->hit_cap = (stat & ST_JACOBI_SWEEPS) != 0;
@@ -739,14 +741,15 @@ bool jacobi_svd_block(fastpi_ctx* hc, float* K, float* V, int n, double* sig, in
   // blocks of 8 columns (16-column panels) with K and V staged; for wider
   // cores (n > ~1 790) only K staged, V streamed from L2 (up to n ~ 2 430:
   // 152 block pairs per round)
-  bool ok = launch_block<16, true>(hc, K, V, n, stats, &ms, &sweeps);
-  if (!ok) ok = launch_block<16, false>(hc, K, V, n, stats, &ms, &sweeps);
+  bool res = false;
+  bool ok = launch_block<16, true>(hc, K, V, n, stats, &ms, &sweeps, &res);
+  if (!ok) ok = launch_block<16, false>(hc, K, V, n, stats, &ms, &sweeps, &res);
   if (!ok) return false;
   std::vector<JacobiProblem<float>> pr(1);
   pr[0] = JacobiProblem<float>{K, V, n, n, n, n};
   jacobi_sort_columns<float>(hc, pr, sig, perm);
   const double dn = n;
-  note_jacobi(ms, double(sweeps) * (dn * (dn - 1) / 2) * (12 * dn + 6 * dn));
+  note_svd(SVD_CORE32, ms, 12 * dn * dn * dn, double(sweeps) * (dn * (dn - 1) / 2) * (12 * dn + 6 * dn), res);
   return true;
 }
 

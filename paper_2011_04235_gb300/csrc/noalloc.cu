@@ -9,12 +9,19 @@
 // library holds that array until the process exits.
 //
 // The array's host-side name is only a stand-in for the symbol, not a device
-// address, so the host never passes it to a kernel: on the first call on each
-// device (with that device current) the entry point looks the address up with
-// cudaGetSymbolAddress, checks the result, caches it per device and passes it
-// to the kernels.  All calls share the array: calls that overlap on the GPU (for
-// example on two streams) race on it.  Every call overwrites all the entries
-// it reads, so nothing has to be cleared between calls.
+// address, so the host never passes it to a kernel.  Every call runs on the
+// device of the caller's stream (made current for the call).  The first call
+// on each device is its set-up: with that device current it looks the address
+// up with cudaGetSymbolAddress, checks the result and caches it for that
+// device; every call passes the cached address to the kernels.  With CUDA's
+// lazy module loading that first call is also the one that loads this file's
+// kernels and the array onto the device, which takes device memory once: make
+// one call (m = 0 is enough) before the memory budget is locked.  A
+// cudaDeviceReset invalidates the cached address together with everything else
+// the process held on that device; do not call this entry point on a device
+// after resetting it.  All calls share the array: calls that overlap on the
+// GPU (for example on two streams) race on it.  Every call overwrites all the
+// entries it reads, so nothing has to be cleared between calls.
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -30,6 +37,14 @@ static __device__ __align__(256) double g_residual_scratch[kMaxRows + 1];
 constexpr int kMaxDevices = 64;
 double* g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
+
+// Restores the caller's current device when the call returns.
+struct DeviceGuard {
+  int saved = -1;
+  ~DeviceGuard() {
+    if (saved >= 0) (void)cudaSetDevice(saved);
+  }
+};
 
 // per-row squared residual of A Z - Y (warp per row)
 __global__ void k_rows(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
@@ -73,8 +88,22 @@ extern "C" fastpi_status fastpi_residual_noalloc(int64_t m, int64_t n, const int
   if (!out || !rowptr || m < 0 || n < 0 || L < 0 || ldy < L || ldz < L) return FASTPI_ERR_ARG;
   if (m > kMaxRows) return FASTPI_ERR_ARG;   // more rows than the static scratch holds
   if (m > 0 && L > 0 && (!Y || !Z || !colind || !val)) return FASTPI_ERR_ARG;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FASTPI_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // the stream's own device (the legacy default stream belongs to the current one)
+  DeviceGuard guard;
+  int cur = 0, dev = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) return FASTPI_ERR_CUDA;
+  if (st == nullptr) {
+    dev = cur;
+  } else if (cudaStreamGetDevice(st, &dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return FASTPI_ERR_ARG;
+  }
+  if (dev != cur) {
+    if (cudaSetDevice(dev) != cudaSuccess) return FASTPI_ERR_CUDA;
+    guard.saved = cur;
+  }
+  if (dev < 0 || dev >= kMaxDevices) return FASTPI_ERR_CUDA;
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_scratch_mu);
@@ -88,7 +117,6 @@ extern "C" fastpi_status fastpi_residual_noalloc(int64_t m, int64_t n, const int
     }
     scratch = g_scratch_ptr[dev];
   }
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const int64_t rows = (m > 0 && L > 0) ? m : 0;
   if (rows > 0) {
     const unsigned grid = unsigned((rows * 32 + 255) / 256);

@@ -14,8 +14,9 @@ void fail(fastpi_status s, const std::string& msg) { throw Error{s, msg}; }
 namespace {
 std::atomic<uint64_t> g_launches{0};
 std::mutex g_prof_mu;
-uint64_t g_jacobi_launches = 0;
-double g_jacobi_ms = 0, g_jacobi_flops = 0;
+uint64_t g_svd_launches[3] = {0, 0, 0};
+double g_svd_ms[3] = {0, 0, 0}, g_svd_flops[3] = {0, 0, 0}, g_svd_flops_rot[3] = {0, 0, 0};
+uint64_t g_core_resident = 0;
 }  // namespace
 
 void note_launch(const char* file, int line) {
@@ -23,26 +24,36 @@ void note_launch(const char* file, int line) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
-void note_jacobi(double ms, double flops) {
+void note_svd(int kind, double ms, double flops_model, double flops_rot, bool resident) {
+  if (kind < 0 || kind > 2) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  ++g_jacobi_launches;
-  g_jacobi_ms += ms;
-  g_jacobi_flops += flops;
+  ++g_svd_launches[kind];
+  g_svd_ms[kind] += ms;
+  g_svd_flops[kind] += flops_model;
+  g_svd_flops_rot[kind] += flops_rot;
+  if (resident) ++g_core_resident;
 }
 
 void read_counters(fastpi_counters* out) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   out->kernel_launches = g_launches.load();
-  out->jacobi_launches = g_jacobi_launches;
-  out->jacobi_ms = g_jacobi_ms;
-  out->jacobi_flops = g_jacobi_flops;
+  for (int k = 0; k < 3; ++k) {
+    out->svd_launches[k] = g_svd_launches[k];
+    out->svd_ms[k] = g_svd_ms[k];
+    out->svd_flops[k] = g_svd_flops[k];
+    out->svd_flops_rot[k] = g_svd_flops_rot[k];
+  }
+  out->core_resident_launches = g_core_resident;
 }
 
 void reset_counters() {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   g_launches.store(0);
-  g_jacobi_launches = 0;
-  g_jacobi_ms = g_jacobi_flops = 0;
+  for (int k = 0; k < 3; ++k) {
+    g_svd_launches[k] = 0;
+    g_svd_ms[k] = g_svd_flops[k] = g_svd_flops_rot[k] = 0;
+  }
+  g_core_resident = 0;
 }
 
 void allow_max_dynamic_smem(const void* func) {

@@ -2,14 +2,15 @@
 tooling around the library, not part of the method's hot path).
 
 - ``reconstruction_error``: ||A - U diag(S) V^T||_F / ||A||_F, the accuracy
-  measure of the low-rank approximation behind the pseudoinverse (Section 4).
+  measure of the low-rank approximation behind the pseudoinverse (Section 4),
+  computed by the library (fastpi_recon_error).
 - ``precision_at_k``: P@k of multi-label scores, the measure of the
   multi-label linear regression application (Application 1, Section 4): the
   fraction of the k highest-scored labels of a row that are true labels,
   averaged over rows.
 - ``heldout_eval``: the application's protocol on a seeded 90% / 10% split of
-  the rows: Z = A_train^+ Y_train from the library, scores A_test Z, P@k on
-  the held-out rows.
+  the rows: Z = A_train^+ Y_train and the scores A_test Z (fastpi_spmm) from
+  the library, P@k on the held-out rows.
 """
 from __future__ import annotations
 
@@ -19,25 +20,10 @@ import torch
 from . import fastpi
 
 
-def reconstruction_error(h: "fastpi.FastPI", rowptr, col, val) -> float:
-    """||A - U S V^T||_F / ||A||_F from the handle's factors (U, V orthonormal
-    up to rounding):  ||A||^2 - 2 sum_i s_i u_i^T A v_i + sum_i s_i^2  (A in
-    CSR, host arrays)."""
-    dev = h.device
-    A = torch.sparse_csr_tensor(torch.as_tensor(np.asarray(rowptr, dtype=np.int64)),
-                                torch.as_tensor(np.asarray(col, dtype=np.int64)),
-                                torch.as_tensor(np.asarray(val, dtype=np.float64)),
-                                size=(h.m, h.n)).to(dev)
-    U, V = h.U(), h.V()
-    S = torch.from_numpy(h.S()).to(dev)
-    AV = A @ V                                   # m x r
-    cross = (U * AV).sum(dim=0)                  # u_i^T A v_i
-    a2 = float(np.sum(np.asarray(val, dtype=np.float64) ** 2))
-    # ||A - U S V^T||^2 with the Gram of the factors, exact also when U, V
-    # are orthonormal only to rounding
-    G = (U.T @ U) * (V.T @ V)
-    e2 = a2 - 2.0 * float((S * cross).sum()) + float(S @ G @ S)
-    return float(np.sqrt(max(e2, 0.0) / a2))
+def reconstruction_error(h: "fastpi.FastPI") -> float:
+    """||A - U S V^T||_F / ||A||_F from the handle's factors (computed by the
+    library, fastpi_recon_error)."""
+    return h.recon_error()
 
 
 def precision_at_k(scores: np.ndarray, labels: np.ndarray, k: int) -> float:
@@ -77,11 +63,11 @@ def heldout_eval(m: int, n: int, rowptr, col, val, Y: np.ndarray, r: int, k_hub:
     h = fastpi.FastPI(train.size, n, *tr, device=device)
     h.factor(r, k_hub, precision, chunk, chunk)
     Z = h.apply(torch.from_numpy(np.ascontiguousarray(Y[train])).to(device))
-    A_te = torch.sparse_csr_tensor(torch.as_tensor(te[0]), torch.as_tensor(te[1].astype(np.int64)),
-                                   torch.as_tensor(te[2]), size=(test.size, n)).to(device)
-    scores = (A_te @ Z).cpu().numpy()
+    g = fastpi.FastPI(test.size, n, *te, device=device)   # held-out rows: scores A_test Z (fastpi_spmm)
+    scores = g.spmm(Z).cpu().numpy()
+    g.close()
     out = {f"P@{k}": precision_at_k(scores, Y[test], k) for k in ks}
-    out["reconstruction_error"] = reconstruction_error(h, *tr)
+    out["reconstruction_error"] = reconstruction_error(h)
     out["rank"] = h.rank
     out["train_rows"], out["test_rows"] = int(train.size), int(test.size)
     h.close()

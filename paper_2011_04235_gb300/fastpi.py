@@ -26,8 +26,8 @@ STATUS = {0: "FASTPI_OK", 1: "FASTPI_ERR_ARG", 2: "FASTPI_ERR_CSR", 3: "FASTPI_E
 
 # every symbol the header declares
 SYMBOLS = ["fastpi_create", "fastpi_create_from_factors", "fastpi_truncate", "fastpi_factor",
-           "fastpi_factor_batched", "fastpi_reorder", "fastpi_apply", "fastpi_apply_host", "fastpi_apply_csr",
-           "fastpi_residual", "fastpi_residual_noalloc", "fastpi_get_rank", "fastpi_get_S", "fastpi_get_U",
+           "fastpi_factor_batched", "fastpi_reorder", "fastpi_block_svd", "fastpi_apply", "fastpi_apply_host", "fastpi_apply_csr",
+           "fastpi_residual", "fastpi_residual_noalloc", "fastpi_spmm", "fastpi_recon_error", "fastpi_get_rank", "fastpi_get_S", "fastpi_get_U",
            "fastpi_get_V",
            "fastpi_get_perm", "fastpi_get_blocks", "fastpi_get_info", "fastpi_get_counters",
            "fastpi_reset_counters", "fastpi_gemm_f32", "fastpi_last_error", "fastpi_destroy"]
@@ -53,14 +53,25 @@ class Info(C.Structure):
 
 
 class Counters(C.Structure):
-    _fields_ = [("kernel_launches", C.c_uint64), ("jacobi_launches", C.c_uint64), ("jacobi_ms", C.c_double),
-                ("jacobi_flops", C.c_double)]
+    _fields_ = [("kernel_launches", C.c_uint64), ("svd_launches", C.c_uint64 * 3), ("svd_ms", C.c_double * 3),
+                ("svd_flops", C.c_double * 3), ("svd_flops_rot", C.c_double * 3),
+                ("core_resident_launches", C.c_uint64)]
+
+
+SVD_KINDS = ("blocks", "core32", "core64")
 
 
 def counters() -> dict:
+    """Process counters: kernel launches, and per SVD kind ("blocks": Eq. 1;
+    "core32" / "core64": update cores) launches, event-timed ms, model flops
+    and rotation flops."""
     c = Counters()
     _check(lib().fastpi_get_counters(C.byref(c)))
-    return {f[0]: getattr(c, f[0]) for f in c._fields_}
+    out = {"kernel_launches": c.kernel_launches, "core_resident_launches": c.core_resident_launches}
+    for i, kind in enumerate(SVD_KINDS):
+        out[kind] = {"launches": c.svd_launches[i], "ms": c.svd_ms[i], "flops": c.svd_flops[i],
+                     "flops_rot": c.svd_flops_rot[i]}
+    return out
 
 
 def reset_counters() -> None:
@@ -70,11 +81,30 @@ def reset_counters() -> None:
 def residual_noalloc(m: int, n: int, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,
                      Y: torch.Tensor, Z: torch.Tensor) -> float:
     """|A Z - Y|_F through fastpi_residual_noalloc (device tensors, no allocation
-    inside the library; A in CSR: rowptr int64, col int32, val float64)."""
+    inside the library; A in CSR: rowptr int64 of m + 1 entries, col int32 and
+    val float64 of equal length; Y m x L and Z n x L float64, row-major).  All
+    tensors must be CUDA tensors on one device; anything else raises
+    ValueError before the library is called (the library reads these buffers
+    by the given sizes without checking them)."""
+    m, n = int(m), int(n)
+    for name, t, dt in (("rowptr", rowptr, torch.int64), ("col", col, torch.int32), ("val", val, torch.float64)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.dim() == 1):
+            raise ValueError(f"{name} must be a 1-D CUDA {dt} tensor")
+    if rowptr.numel() != m + 1:
+        raise ValueError(f"rowptr must have m + 1 = {m + 1} entries")
+    if col.numel() != val.numel():
+        raise ValueError("col and val must have the same length")
+    Y = _dense_dev(Y, m, "Y")
+    Z = _dense_dev(Z, n, "Z")
+    if Y.shape[1] != Z.shape[1]:
+        raise ValueError("Y and Z must have the same number of columns")
+    if len({t.device for t in (rowptr, col, val, Y, Z)}) != 1:
+        raise ValueError("rowptr, col, val, Y and Z must be on one device")
+    rowptr, col, val = rowptr.contiguous(), col.contiguous(), val.contiguous()
     out = C.c_double()
     st = torch.cuda.current_stream(Y.device).cuda_stream
     with torch.cuda.device(Y.device):
-        _check(lib().fastpi_residual_noalloc(int(m), int(n), _ptr(rowptr), _ptr(col), _ptr(val), _ptr(Y),
+        _check(lib().fastpi_residual_noalloc(m, n, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(Y),
                                              Y.shape[1], Y.stride(0), _ptr(Z), Z.stride(0), C.byref(out), st))
     return out.value
 
@@ -126,6 +156,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fastpi_create": ([C.POINTER(p), i64, i64, i64, vp, vp, vp, i32, vp], i32),
         "fastpi_factor": ([p, i64, dbl, i32, i64, i64], i32),
         "fastpi_reorder": ([p, dbl], i32),
+        "fastpi_block_svd": ([p, i64, dbl, i32, vp, i64, C.POINTER(i64)], i32),
         "fastpi_create_from_factors": ([C.POINTER(p), i64, i64, i64, vp, vp, i64, vp, i64, i32, i32, vp], i32),
         "fastpi_truncate": ([p, i64], i32),
         "fastpi_factor_batched": ([vp, i32, vp, dbl, i32, i64, i64, i32, vp], i32),
@@ -133,6 +164,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fastpi_apply_host": ([p, vp, i64, i64, vp, i64], i32),
         "fastpi_apply_csr": ([p, i64, i64, vp, vp, vp, vp, i64], i32),
         "fastpi_residual": ([p, vp, i64, i64, vp, i64, C.POINTER(dbl)], i32),
+        "fastpi_spmm": ([p, vp, i64, i64, vp, i64], i32),
+        "fastpi_recon_error": ([p, C.POINTER(dbl)], i32),
         "fastpi_residual_noalloc": ([i64, i64, vp, vp, vp, vp, i64, i64, vp, i64, C.POINTER(dbl), vp], i32),
         "fastpi_gemm_f32": ([i32, i32, i64, i64, i64, C.c_float, vp, i64, vp, i64, C.c_float, vp, i64, i32, vp],
                             i32),
@@ -283,6 +316,18 @@ class FastPI:
             _check(lib().fastpi_reorder(self._h, float(k)), self._h)
         return self
 
+    def block_svd(self, r: int, k: float, precision="fp64") -> np.ndarray:
+        """Eq. 1 alone (Algorithm 2, then the SVD of every A11 block): the kept
+        block singular values, block by block, descending within a block."""
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        S = C.c_int64()
+        cap = max(self.n, 1)
+        sig = np.empty(cap, dtype=np.float64)
+        with torch.cuda.device(self.device):
+            _check(lib().fastpi_block_svd(self._h, int(r), float(k), prec, sig.ctypes.data, cap, C.byref(S)),
+                   self._h)
+        return sig[:S.value].copy()
+
     def apply(self, Y: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         Y = _dense_dev(Y, self.m, "Y")
         L = Y.shape[1]
@@ -332,6 +377,21 @@ class FastPI:
         with torch.cuda.device(self.device):
             _check(lib().fastpi_residual(self._h, _ptr(Y), Y.shape[1], Y.stride(0), _ptr(Z), Z.stride(0),
                                          C.byref(out)), self._h)
+        return out.value
+
+    def spmm(self, X: torch.Tensor) -> torch.Tensor:
+        """A X (m x L) for X n x L (CUDA float64)."""
+        X = _dense_dev(X, self.n, "X")
+        out = torch.empty((self.m, X.shape[1]), dtype=torch.float64, device=X.device)
+        with torch.cuda.device(self.device):
+            _check(lib().fastpi_spmm(self._h, _ptr(X), X.shape[1], X.stride(0), _ptr(out), out.stride(0)), self._h)
+        return out
+
+    def recon_error(self) -> float:
+        """|A - U diag(S) V^T|_F / |A|_F from the stored factors (FP64, on the device)."""
+        out = C.c_double()
+        with torch.cuda.device(self.device):
+            _check(lib().fastpi_recon_error(self._h, C.byref(out)), self._h)
         return out.value
 
     @property

@@ -64,3 +64,31 @@ def test_missing_library_fails_loudly():
     assert not os.path.exists(missing)
     with pytest.raises(ImportError):
         fastpi.load_library(missing)
+
+
+def test_binding_residual_noalloc_checks_arguments():
+    """residual_noalloc refuses, before any pointer reaches the library, the
+    arguments whose sizes or types the C entry point would read past or
+    misread: host tensors, an int32 rowptr, a rowptr of the wrong length,
+    col / val of different lengths, a Y or Z with the wrong row count."""
+    import pytest
+    import torch
+    from paper_2011_04235_gb300 import fastpi
+    m, n = 4, 3
+    rp = torch.tensor([0, 1, 2, 3, 4], dtype=torch.int64)
+    cl = torch.tensor([0, 1, 2, 0], dtype=torch.int32)
+    vl = torch.ones(4, dtype=torch.float64)
+    Y = torch.zeros(m, 2, dtype=torch.float64)
+    Z = torch.zeros(n, 2, dtype=torch.float64)
+    cases = [
+        (rp, cl, vl, Y, Z),                              # host tensors
+        (rp.to(torch.int32), cl, vl, Y, Z),              # rowptr int32
+        (rp[:-1], cl, vl, Y, Z),                         # rowptr of m entries
+        (rp, cl, vl[:-1], Y, Z),                         # col and val lengths differ
+        (rp, cl, vl, Y[:-1], Z),                         # Y with m - 1 rows
+        (rp, cl, vl, Y, Z[:-1]),                         # Z with n - 1 rows
+        (rp, cl.to(torch.int64), vl, Y, Z),              # col int64
+    ]
+    for args in cases:
+        with pytest.raises(ValueError):
+            fastpi.residual_noalloc(m, n, *args)

@@ -32,11 +32,31 @@ def test_reconstruction_error_matches_oracle():
     cfg = w["cfg"]
     h = fp.FastPI(w["m"], w["n"], w["rowptr"], w["col"], w["val"], device="cuda:0")
     h.factor(cfg.r, cfg.k, "fp64", 64, 64)
-    e_gpu = reconstruction_error(h, w["rowptr"], w["col"], w["val"])
+    e_gpu = reconstruction_error(h)
     f = ofp.factor(w["m"], w["n"], w["rowptr"], w["col"], w["val"], cfg.r, cfg.k, chunk_row=64, chunk_col=64)
     A = sp.csr_matrix((w["val"], w["col"], w["rowptr"]), shape=(w["m"], w["n"])).toarray()
     e_ref = np.linalg.norm(A - (f.U * f.S) @ f.V.T) / np.linalg.norm(A)
     assert abs(e_gpu - e_ref) <= 1e-8 * max(e_ref, 1e-300)
+    # the mixed form's factors: FP32 U, V, their reconstruction error within
+    # 1e-3 of the oracle's
+    g = fp.FastPI(w["m"], w["n"], w["rowptr"], w["col"], w["val"], device="cuda:0")
+    g.factor(cfg.r, cfg.k, "mixed", 64, 64)
+    assert abs(reconstruction_error(g) - e_ref) <= 1e-3 * e_ref
+    g.close()
+    h.close()
+
+
+@pytest.mark.gpu
+def test_spmm_matches_scipy():
+    from gpu_common import binding
+    fp = binding()
+    w = workloads.make("small")
+    h = fp.FastPI(w["m"], w["n"], w["rowptr"], w["col"], w["val"], device="cuda:0")
+    X = np.random.default_rng(3).standard_normal((w["n"], 300))
+    got = h.spmm(torch.from_numpy(X).cuda()).cpu().numpy()
+    A = sp.csr_matrix((w["val"], w["col"], w["rowptr"]), shape=(w["m"], w["n"]))
+    ref = A @ X
+    assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref)
     h.close()
 
 

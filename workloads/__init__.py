@@ -164,3 +164,64 @@ def make_tiny_random(m: int, n: int, density: float, rng: np.random.Generator,
     np.add.at(rowptr, rows + 1, 1)
     rowptr = np.cumsum(rowptr)
     return rowptr, cols.astype(np.int32), vals[rows, cols].astype(np.float64)
+
+
+def _coo_to_csr(m: int, rows: np.ndarray, cols: np.ndarray, vals: np.ndarray):
+    """CSR with sorted, duplicate-free columns per row (first occurrence kept)."""
+    keys = rows.astype(np.int64) * (int(cols.max()) + 1 if cols.size else 1) + cols
+    _, first = np.unique(keys, return_index=True)
+    rows, cols, vals = rows[first], cols[first], vals[first]
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    rowptr = np.zeros(m + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    return np.cumsum(rowptr), cols.astype(np.int32), vals.astype(np.float64)
+
+
+def make_long_blocks(seed: int = 0):
+    """A matrix whose hub-and-spoke reordering (k = 0.0006) has long diagonal
+    blocks: spokes of 1500 x 200, 2200 x 150 and 300 x 1500 (random sparse
+    rows of 3 entries, columns of 2 entries for the wide one) and a final giant
+    component that is a star of 3000 rows on one column.  Five dense "hub" rows
+    and two "hub" columns of the highest degrees join everything, so that the
+    first iteration removes exactly them and the star, with a single feature,
+    ends the loop.  Values uniform(0, 1].  Returns (m, n, rowptr, col, val)."""
+    rng = np.random.default_rng(seed)
+    specs = [(1500, 200, "rows"), (2200, 150, "rows"), (300, 1500, "cols")]
+    r0 = 5                       # hub rows first, then the blocks, then the star
+    c0 = 2                       # hub columns first
+    R, Cc = [], []
+    row_ranges, col_ranges = [], []
+    ro, co = r0, c0
+    for mb, nb, kind in specs:
+        if kind == "rows":
+            rr = np.repeat(np.arange(mb), 3)
+            cc = np.concatenate([rng.choice(nb, 3, replace=False) for _ in range(mb)])
+        else:
+            cc = np.repeat(np.arange(nb), 2)
+            rr = np.concatenate([rng.choice(mb, 2, replace=False) for _ in range(nb)])
+        R.append(rr + ro)
+        Cc.append(cc + co)
+        row_ranges.append((ro, ro + mb))
+        col_ranges.append((co, co + nb))
+        ro += mb
+        co += nb
+    star_rows = np.arange(ro, ro + 3000)
+    star_col = co
+    R.append(star_rows)
+    Cc.append(np.full(3000, star_col))
+    m, n = ro + 3000, co + 1
+    # hub rows: 600 random columns each; hub columns: 4000 random rows each
+    for i in range(r0):
+        R.append(np.full(600, i))
+        Cc.append(rng.choice(np.arange(c0, n), 600, replace=False))
+    for j in range(c0):
+        R.append(rng.choice(np.arange(r0, m), 4000, replace=False))
+        Cc.append(np.full(4000, j))
+    rows = np.concatenate(R)
+    cols = np.concatenate(Cc)
+    vals = 1.0 - rng.random(rows.size)
+    # shuffle row and column ids so nothing is pre-sorted
+    prow, pcol = rng.permutation(m), rng.permutation(n)
+    rowptr, col, val = _coo_to_csr(m, prow[rows], pcol[cols], vals)
+    return m, n, rowptr, col, val
