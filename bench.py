@@ -35,11 +35,40 @@ import workloads  # noqa: E402
 
 METRIC = "A†Y factor+solve seconds and GFLOP/s at rank r, mixed vs FP64 at same residual"
 WORKLOAD = "medium"
-CHUNK = 256
+TUNING = os.path.join(ROOT, "paper_2011_04235_gb300", "tuning.txt")
+
+
+def table_chunk(prec_id: int, phase: int, k_target: int, default: int = 256) -> int:
+    """The append chunk the library takes for chunk 0: the tuning table's
+    value for this precision, phase and target rank (first matching line),
+    else 256."""
+    try:
+        lines = open(TUNING).read().splitlines()
+    except OSError:
+        return default
+    for ln in lines:
+        f = ln.split("#")[0].split()
+        if len(f) == 5 and f[0] == "chunk" and int(f[1]) == prec_id and int(f[2]) == phase and k_target <= int(f[3]):
+            return int(f[4])
+    return default
+
+
+def oracle_chunk_schedule(w):
+    """(chunk_row, chunk_col) of the mixed form's autotuned schedule, from the
+    phases' target ranks (Algorithm 2 on the host, Eq. 1's s_i), for the CPU
+    arm that runs without the library."""
+    from oracle.reorder import reorder
+    m, n, cfg = w["m"], w["n"], w["cfg"]
+    R = reorder(m, n, w["rowptr"], w["col"], cfg.k)
+    mb, nb = np.diff(R.row_off), np.diff(R.col_off)
+    S = int(np.sum(np.minimum(np.minimum((cfg.r * nb + n - 1) // n, mb), nb)))
+    s_row = min((cfg.r * R.n1 + n - 1) // n, S + (m - R.m1), R.n1)
+    rank = min(cfg.r, m, s_row + (n - R.n1))
+    return table_chunk(1, 0, s_row), table_chunk(1, 1, rank)
 
 
 # ----------------------------------------------------------------------------- flop model
-def flop_model(m, n, nnz_a21, nnz_t, m1, n1, m2, n2, row_off, col_off, r, L, chunk):
+def flop_model(m, n, nnz_a21, nnz_t, m1, n1, m2, n2, row_off, col_off, r, L, chunk, chunk_col=None):
     """Flops of FastPI factor + solve from the method's shapes (Algorithm 1 with
     the chunked updates of Eqs. 2 / 3).  Dense SVD of a p x q matrix (p >= q)
     with vectors counts 4 p q^2 + 8 q^3.  One append of c columns to a rank-k
@@ -48,6 +77,8 @@ def flop_model(m, n, nnz_a21, nnz_t, m1, n1, m2, n2, row_off, col_off, r, L, chu
     (two Gram matrices, two triangular applies) + 12 (k + c)^3 (core SVD)
     + 2 p (k + c) kk + 2 q k kk (rotations)."""
     ceil_a = lambda x: (r * x + n - 1) // n
+    chunk_row = chunk
+    chunk_col = chunk if chunk_col is None else chunk_col
     mb = np.diff(row_off)
     nb = np.diff(col_off)
     sb = np.minimum(np.minimum(ceil_a(nb), mb), nb)
@@ -57,7 +88,7 @@ def flop_model(m, n, nnz_a21, nnz_t, m1, n1, m2, n2, row_off, col_off, r, L, chu
     F = float(np.sum(4 * p[live] * q[live] ** 2 + 8 * q[live] ** 3))
     S = int(sb.sum())
 
-    def phase(pdim, k, q0, total, target, nnz_total):
+    def phase(pdim, k, q0, total, target, nnz_total, chunk):
         nonlocal F
         qrows = q0
         for a in range(0, total, chunk):
@@ -73,17 +104,17 @@ def flop_model(m, n, nnz_a21, nnz_t, m1, n1, m2, n2, row_off, col_off, r, L, chu
     s = int(min(ceil_a(n1), S + m2, n1))
     # with several appends the row phase starts from the s largest block
     # triplets (its coefficient matrix keeps the S block rows)
-    k0 = s if (chunk < m2 and S > s) else S
-    s = phase(n1, k0, S, m2, s, nnz_a21)
+    k0 = s if (chunk_row < m2 and S > s) else S
+    s = phase(n1, k0, S, m2, s, nnz_a21, chunk_row)
     F += 2.0 * float(np.sum(mb * sb)) * s            # U_row = bdiag(U1, I) W
     rr = int(min(r, m, s + n2))
-    rr = phase(m, s, s, n2, rr, nnz_t)
+    rr = phase(m, s, s, n2, rr, nnz_t, chunk_col)
     F += 2.0 * n1 * s * rr                           # V = [[V_row W_top], [W_bot]]
     F += 2.0 * m * rr * L + 2.0 * n * rr * L         # Z = V Sigma^+ (U^T Y)
     return F
 
 
-def workload_flops(w, reo_row_order, reo_col_order, row_off, col_off, m1, n1, chunk):
+def workload_flops(w, reo_row_order, reo_col_order, row_off, col_off, m1, n1, chunk, chunk_col=None):
     m, n, cfg = w["m"], w["n"], w["cfg"]
     rows = np.repeat(np.arange(m), np.diff(w["rowptr"]))
     pos_r = np.empty(m, dtype=np.int64)
@@ -95,7 +126,7 @@ def workload_flops(w, reo_row_order, reo_col_order, row_off, col_off, m1, n1, ch
     nnz_t = int(np.count_nonzero(nc >= n1))
     L = w["Y"].shape[1]
     return flop_model(m, n, nnz_a21, nnz_t, m1, n1, m - m1, n - n1, np.asarray(row_off), np.asarray(col_off),
-                      cfg.r, L, chunk)
+                      cfg.r, L, chunk, chunk_col)
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -156,7 +187,7 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU oracle sample
-def oracle_sample(w, budget_s: float = 60.0):
+def oracle_sample(w, chunks, budget_s: float = 60.0):
     """Time the FP64 CPU oracle, as it stands, on the whole workload: reorder,
     block SVD, row and column updates with the same chunk schedule, and the
     apply.  Returns (GFLOP/s under the bench's flop model, seconds,
@@ -165,21 +196,22 @@ def oracle_sample(w, budget_s: float = 60.0):
 
     cfg = w["cfg"]
     t0 = time.perf_counter()
-    f = ofp.factor(w["m"], w["n"], w["rowptr"], w["col"], w["val"], cfg.r, cfg.k, chunk_row=CHUNK, chunk_col=CHUNK)
+    cr, cc = chunks
+    f = ofp.factor(w["m"], w["n"], w["rowptr"], w["col"], w["val"], cfg.r, cfg.k, chunk_row=cr, chunk_col=cc)
     Zo = ofp.apply(f, w["Y"])
     secs = time.perf_counter() - t0
     import scipy.sparse as sp
     A = sp.csr_matrix((w["val"], w["col"], w["rowptr"]), shape=(w["m"], w["n"]))
     res_o = float(np.linalg.norm(A @ Zo - w["Y"]))
     reo = f.reo
-    F = workload_flops(w, reo.row_order, reo.col_order, reo.row_off, reo.col_off, reo.m1, reo.n1, CHUNK)
+    F = workload_flops(w, reo.row_order, reo.col_order, reo.row_off, reo.col_off, reo.m1, reo.n1, cr, cc)
     try:
         from threadpoolctl import threadpool_info
         threads = max((d.get("num_threads", 1) for d in threadpool_info()), default=1)
     except Exception:
         threads = len(os.sched_getaffinity(0))
     desc = (f"FP64 oracle (NumPy/SciPy LAPACK) on the whole {cfg.name} workload: reorder, block SVD, "
-            f"row and column updates with chunk {CHUNK}, apply; flops by the bench's flop model")
+            f"row and column updates with chunks {cr} / {cc}, apply; flops by the bench's flop model")
     return F / secs / 1e9, secs, desc, threads, np.asarray(f.S), res_o
 
 
@@ -218,11 +250,13 @@ def factor_accuracy(h):
     return out
 
 
-def bench_config(w):
+def bench_config(w, chunks):
     """The workload description shared by both arms of the bench."""
     cfg = w["cfg"]
     return {"workload": cfg.name, "m": int(w["m"]), "n": int(w["n"]), "nnz": int(w["col"].size), "r": cfg.r,
-            "k": cfg.k, "L": int(cfg.L), "chunk": CHUNK, "gamma": cfg.gamma, "seed": 0,
+            "k": cfg.k, "L": int(cfg.L), "chunk": {"row": int(chunks[0]), "col": int(chunks[1]),
+                                                   "source": "autotuned (chunk 0: the library's tuning table)"},
+            "gamma": cfg.gamma, "seed": 0,
             "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
 
 
@@ -258,19 +292,20 @@ def main():
         if rank != 0:
             return
         w = workloads.make(WORKLOAD)
+        chunks = oracle_chunk_schedule(w)
         vals, secs = [], []
         desc, threads = "", 1
         for _ in range(args.warmup):        # untimed, as for the GPU arm
-            oracle_sample(w, budget_s=20.0)
+            oracle_sample(w, chunks, budget_s=20.0)
         for _ in range(args.steps):
-            g, s, desc, threads, _, _ = oracle_sample(w, budget_s=20.0)
+            g, s, desc, threads, _, _ = oracle_sample(w, chunks, budget_s=20.0)
             vals.append(g)
             secs.append(s)
         v = statistics.mean(vals)
         out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GFLOP/s", "n_gpus": args.gpus,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(secs),
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-               "data": "synthetic", "config": bench_config(w),
+               "data": "synthetic", "config": bench_config(w, chunks),
                "precision": "FP64 CPU oracle (NumPy / SciPy LAPACK)",
                "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
                                 "sample": desc},
@@ -310,8 +345,11 @@ def main():
     h = fastpi.FastPI(m, n, rp, cl, vl, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > 129 MB L2
 
+    chunks = [0, 0]   # mixed: chunk 0, the library's autotuned chunks
+
     def step(prec):
-        h.factor(cfg.r, cfg.k, prec, CHUNK, CHUNK)
+        cr, cc = chunks if prec == "fp64" else (0, 0)
+        h.factor(cfg.r, cfg.k, prec, cr, cc)
         h.apply(Yd, out=Z)
 
     def timed(prec, steps, warmup, sampler=None):
@@ -347,10 +385,11 @@ def main():
     t_mixed, cnt_mixed, clocks = timed("mixed", args.steps, max(args.warmup, 3), sampler)
     res_mixed = h.residual(Yd, Z)
     info = h.info()
+    chunks[:] = [info["chunk_row"], info["chunk_col"]]   # the FP64 form and the oracle take the same schedule
     acc = {"mixed": factor_accuracy(h), "fp64": None}
     ro, co, _, _ = h.perm()
     bro, bco = h.blocks()
-    F = workload_flops(w, ro, co, bro, bco, info["m1"], info["n1"], CHUNK)
+    F = workload_flops(w, ro, co, bro, bco, info["m1"], info["n1"], chunks[0], chunks[1])
     # FP64 form at the same chunk schedule
     t64, _, _ = timed("fp64", max(args.fp64_steps, 1), 1)
     res64 = h.residual(Yd, Z)
@@ -369,7 +408,7 @@ def main():
             t0 = time.perf_counter()
             hh = fastpi.FastPI(m, n, w["rowptr"], w["col"], w["val"], device=dev)
             tc = time.perf_counter()        # fastpi_create returns after its upload, check and CSC build
-            hh.factor(cfg.r, cfg.k, "mixed", CHUNK, CHUNK)
+            hh.factor(cfg.r, cfg.k, "mixed", 0, 0)
             Zh = hh.apply_host(w["Y"])
             t1 = time.perf_counter()
             hh.close()
@@ -418,7 +457,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:   # the host-core baseline: N = 1 only
-        g, s, desc, threads, S_o, res_o = oracle_sample(w, budget_s=20.0)
+        g, s, desc, threads, S_o, res_o = oracle_sample(w, chunks, budget_s=20.0)
         cpu = {"value": g, "unit": "GFLOP/s", "cores": threads, "kind": "oracle", "sample": desc, "seconds": s}
         for form, res in (("mixed", res_mixed), ("fp64", res64)):
             S_g = acc[form].pop("S")
@@ -433,7 +472,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": 1000 * sec_mixed, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": bench_config(w),
+            "config": bench_config(w, chunks),
             "precision": "mixed: FP32 storage, TF32 tensor-core products (split hi/lo, 3 passes) with FP32 "
                          "accumulation, FP64-accumulated Gram and FP64 Cholesky, FP32 block-Jacobi core SVD",
             "mixed": {"seconds": sec_mixed, "gflops": F / sec_mixed / 1e9, "residual": res_mixed,

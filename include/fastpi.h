@@ -95,9 +95,10 @@ fastpi_status fastpi_create(fastpi_t* out, int64_t m, int64_t n, int64_t nnz,
  *   k:     hub selection ratio, 0 < k < 1.
  *   prec:  FASTPI_FP64 or FASTPI_MIXED_TF32.
  *   chunk_row, chunk_col: border rows of A21 / columns of T appended per
- *          incremental step (0 = library default, 256; >= the border size gives
+ *          incremental step (0 = autotuned: the tuning table's value for the
+ *          phase's target rank, 256 without a table; >= the border size gives
  *          the single-shot form of Eqs. 2 and 3).  Each step truncates to the
- *          phase's target rank.
+ *          phase's target rank; fastpi_get_info reports the chunks used.
  * Re-factoring a handle replaces the previous factors.
  */
 fastpi_status fastpi_factor(fastpi_t h, int64_t r, double k, fastpi_precision prec,
@@ -315,6 +316,42 @@ void fastpi_reset_counters(void);
 fastpi_status fastpi_gemm_f32(int ta, int tb, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
                               int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
                               int engine, void* cuda_stream);
+
+/* Diagnostic entry point (no citation: it exposes the FP32 SVD of the
+ * incremental-update cores of Eqs. 2 and 3 -- block one-sided Jacobi -- so
+ * that it can be checked and tuned on its own).  K: device float32 n x n,
+ * COLUMN-major (ld n), the matrix; overwritten (scratch).  On return S (host
+ * float64[n]) holds the singular values in descending order, U and V (device
+ * float32 n x n, column-major) the left and right singular vectors in that
+ * order (a column of U is zero where its value is zero).  Tiling: panel = 16
+ * or 32 columns per block pair, parts = CTAs of a thread-block cluster that
+ * share a block pair's rows (1..8; 0 picks the largest that keeps one round's
+ * clusters on the SMs); flags: 1 = resident-block schedule, 2 = the Gram
+ * sweep by the whole CTA instead of one warp, 4 = the single-CTA kernel
+ * (panel 16, no clusters).  *sweeps and *ms (may be NULL) receive the sweeps
+ * and the CUDA-event time of the Jacobi kernel.  Errors: FASTPI_ERR_ARG
+ * (sizes, flags, or a tiling that does not fit: shared memory or co-resident
+ * clusters), FASTPI_ERR_NO_CONVERGENCE (sweep cap, or a bounded wait ran
+ * out).  The call synchronises the stream. */
+fastpi_status fastpi_core_svd_f32(int n, float* K, float* U, double* S, float* V, int panel, int parts, int flags,
+                                  int* sweeps, float* ms, void* cuda_stream);
+
+/* Tuning table (no citation: parameters of this implementation, picked on the
+ * GPU by the package's autotuner, python -m paper_2011_04235_gb300.autotune).
+ * A plain-text file of lines
+ *   core   <n_max> <panel> <parts> <resident> <warp>   FP32 core-SVD tiling for n <= n_max
+ *   chunk  <prec> <phase> <k_max> <c>                  appends of c border rows (phase 0) /
+ *                                                      columns (phase 1) when fastpi_factor
+ *                                                      gets chunk 0; prec 0 FP64, 1 mixed
+ *   bucket <prec> <dim_max> <class>                    register-tile class of the batched
+ *                                                      Jacobi of the A11 blocks
+ * The library reads it on first use from $FASTPI_TUNING, else from tuning.txt
+ * beside libfastpi.so, else uses built-in defaults (chunk 256).
+ * fastpi_load_tuning replaces the table with the file at path (NULL: the
+ * built-in defaults), for every handle of the process.  FASTPI_ERR_ARG (and
+ * the reason in fastpi_last_error(NULL)) when the file cannot be read or a
+ * line is malformed; the table is then unchanged. */
+fastpi_status fastpi_load_tuning(const char* path);
 
 /* Message of the last failed call on h (or of the last failed fastpi_create
  * when h is NULL).  Never NULL; valid until the next call on h. */

@@ -10,6 +10,8 @@
 
 #include "dense.cuh"
 #include "factor.cuh"
+#include "jacobi.cuh"
+#include "tuning.cuh"
 
 using namespace fastpi;
 
@@ -448,6 +450,61 @@ fastpi_status fastpi_gemm_f32(int ta, int tb, int64_t M, int64_t N, int64_t K, f
   } catch (const std::exception& e) {
     g_create_error = e.what();
     return FASTPI_ERR_CUDA;
+  }
+  return FASTPI_OK;
+}
+
+fastpi_status fastpi_core_svd_f32(int n, float* K, float* U, double* S, float* V, int panel, int parts, int flags,
+                                  int* sweeps, float* ms, void* cuda_stream) {
+  try {
+    require(n >= 2 && n <= 8192, FASTPI_ERR_ARG, "need 2 <= n <= 8192");
+    require(K && U && S && V, FASTPI_ERR_ARG, "null pointer");
+    require(panel == 16 || panel == 32, FASTPI_ERR_ARG, "panel must be 16 or 32");
+    require(parts >= 0 && parts <= 8, FASTPI_ERR_ARG, "parts must lie in [0, 8]");
+    require((flags & ~7) == 0, FASTPI_ERR_ARG, "unknown flag");
+    require(!((flags & 4) && panel != 16), FASTPI_ERR_ARG, "the single-CTA kernel has panel 16");
+    fastpi_ctx ctx;
+    CK(cudaGetDevice(&ctx.device));
+    CK(cudaDeviceGetAttribute(&ctx.num_sms, cudaDevAttrMultiProcessorCount, ctx.device));
+    ctx.stream = static_cast<cudaStream_t>(cuda_stream);
+    ctx.has_matrix = false;
+    ctx.dstatus = DArr<unsigned>(1, ctx.stream);
+    CoreTiling tl;
+    tl.panel = panel;
+    tl.parts = parts;
+    tl.resident = (flags & 1) != 0;
+    tl.warp_solve = (flags & 2) == 0;
+    tl.single_cta = (flags & 4) != 0;
+    tl.strict = true;
+    DArr<float> J(int64_t(n) * n, ctx.stream);
+    DArr<double> sig(n, ctx.stream);
+    DArr<int32_t> perm(n, ctx.stream);
+    JacobiStats js;
+    float t = 0;
+    int sw = 0;
+    require(jacobi_svd_block(&ctx, K, J.get(), n, sig.get(), perm.get(), &js, &tl, &t, &sw), FASTPI_ERR_ARG,
+            "this tiling does not fit the core (shared memory or co-resident clusters)");
+    core_vectors_f32(&ctx, n, K, J.get(), sig.get(), perm.get(), U, V);
+    CK(cudaMemcpyAsync(S, sig.get(), size_t(n) * 8, cudaMemcpyDeviceToHost, ctx.stream));
+    CK(cudaStreamSynchronize(ctx.stream));
+    if (sweeps) *sweeps = sw;
+    if (ms) *ms = t;
+    require(!js.hit_cap, FASTPI_ERR_NO_CONVERGENCE, "core SVD: sweep cap reached");
+  } catch (const Error& e) {
+    g_create_error = e.msg;
+    return e.status;
+  } catch (const std::exception& e) {
+    g_create_error = e.what();
+    return FASTPI_ERR_CUDA;
+  }
+  return FASTPI_OK;
+}
+
+fastpi_status fastpi_load_tuning(const char* path) {
+  std::string why;
+  if (!load_tuning(path, &why)) {
+    g_create_error = why;
+    return FASTPI_ERR_ARG;
   }
   return FASTPI_OK;
 }

@@ -30,6 +30,7 @@
 #include "dense.cuh"
 #include "factor.cuh"
 #include "jacobi.cuh"
+#include "tuning.cuh"
 
 namespace fastpi {
 namespace {
@@ -1019,7 +1020,8 @@ void factor_impl(fastpi_ctx* h, Factors& F, int64_t r, double kratio, int64_t ch
   JacobiStats bjs = bs.js;
   // Row phase basis: V1 (n1 x k0); U1 packed per block (all S); Sigma1
   const int64_t s_row = std::min<int64_t>({(r * n1 + n - 1) / n, S + m2, n1});
-  const int64_t cr = chunk_row > 0 ? chunk_row : DEFAULT_CHUNK;
+  const int prec_id = sizeof(T) == 8 ? 0 : 1;
+  const int64_t cr = chunk_row > 0 ? chunk_row : tuned_chunk(prec_id, 0, s_row, DEFAULT_CHUNK);
   // Block triplet g (blocks in order, descending within a block) goes to
   // state column pos[g].  With several appends the running SVD of Eq. 2 holds
   // rank s_row between appends and the block SVD is its initial state, so only
@@ -1089,7 +1091,7 @@ void factor_impl(fastpi_ctx* h, Factors& F, int64_t r, double kratio, int64_t ch
   tm.start();
   const int64_t s = rowp.k;
   const int64_t rr = std::min<int64_t>({r, m, s + n2});
-  const int64_t cc = chunk_col > 0 ? chunk_col : DEFAULT_CHUNK;
+  const int64_t cc = chunk_col > 0 ? chunk_col : tuned_chunk(prec_id, 1, rr, DEFAULT_CHUNK);
   const int64_t kmax_c = std::max<int64_t>({s, rr, 1});
   Phase<T> colp(h, m, kmax_c, s + n2, std::min(cc, std::max<int64_t>(n2, 1)),
                 sizeof(T) == 8 ? DROP_TOL_FP64 : DROP_TOL_MIXED);

@@ -22,6 +22,7 @@
 #include <cmath>
 
 #include "jacobi.cuh"
+#include "tuning.cuh"
 
 namespace fastpi {
 namespace {
@@ -375,7 +376,7 @@ template <> struct Eps<float> { static constexpr double v = 1.1920928955078125e-
 // outputs at sig / perm + out_off[b].
 template <typename T>
 JacobiStats run_bucket(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& probs,
-                       const std::vector<int64_t>& out_off, double* sig, int32_t* perm, int kind) {
+                       const std::vector<int64_t>& out_off, double* sig, int32_t* perm, int kind, int cls) {
   JacobiStats stats;
   const int nprob = int(probs.size());
   if (nprob == 0) return stats;
@@ -439,21 +440,21 @@ JacobiStats run_bucket(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& probs
   // smallest of {8, 16, 32, 44} that holds the longest column.  FP64: the
   // FP64 rate per SM is low, so a pair is shared by a team of 2 or 4 warps
   // (one team per CTA, spreading pairs over the SMs) holding 16 values per lane.
-  const int maxdim = std::max(maxp, maxq);
+  // the kernel variant of the bucket's register-tile class (tile_class; the
+  // tuning table may put small problems in a larger class)
   void* kern = nullptr;
   int bs = 256, pairs_per_cta = 8;
   if constexpr (sizeof(T) == 4) {
-    const int need = (maxdim + 31) / 32;
-    kern = (void*)k_jacobi<T, 8, 1>;   // also the kernel for long columns (two-pass path)
-    if (need > 8 && need <= 16) kern = (void*)k_jacobi<T, 16, 1>;
-    if (need > 16 && need <= 32) kern = (void*)k_jacobi<T, 32, 1>;
-    if (need > 32 && need <= 44) kern = (void*)k_jacobi<T, 44, 1>;
+    kern = (void*)k_jacobi<T, 8, 1>;   // classes 0 and 4 (long columns: the two-pass path)
+    if (cls == 1) kern = (void*)k_jacobi<T, 16, 1>;
+    if (cls == 2) kern = (void*)k_jacobi<T, 32, 1>;
+    if (cls == 3) kern = (void*)k_jacobi<T, 44, 1>;
   } else {
     pairs_per_cta = 1;
-    if (maxdim <= 64 * 8) {
+    if (cls == 0) {
       kern = (void*)k_jacobi<T, 8, 2>;
       bs = 64;
-    } else if (maxdim <= 64 * 16) {
+    } else if (cls == 1) {
       kern = (void*)k_jacobi<T, 16, 2>;
       bs = 64;
     } else {
@@ -548,14 +549,15 @@ JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>
   std::vector<int64_t> off[NCLASS];
   int64_t soff = 0;
   for (int b = 0; b < nprob; ++b) {
-    const int c = tile_class<T>(probs[b]);
+    const int c = tuned_bucket_class(sizeof(T) == 8 ? 0 : 1, std::max(probs[b].p, probs[b].q),
+                                     tile_class<T>(probs[b]));
     bucket[c].push_back(probs[b]);
     off[c].push_back(soff);
     soff += probs[b].q;
   }
   for (int c = 0; c < NCLASS; ++c) {
     if (bucket[c].empty()) continue;
-    const JacobiStats js = run_bucket<T>(h, bucket[c], off[c], sig, perm, kind);
+    const JacobiStats js = run_bucket<T>(h, bucket[c], off[c], sig, perm, kind, c);
     stats.max_sweeps_used = std::max(stats.max_sweeps_used, js.max_sweeps_used);
     stats.hit_cap = stats.hit_cap || js.hit_cap;
   }

@@ -40,6 +40,31 @@ void jacobi_sort_columns(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& pro
 // (V = J, n x n col-major, ld n); returns false, having
 // done nothing, when a block pair's panels do not fit in one CTA's shared
 // memory or the block pairs of a round exceed the co-resident CTAs.
-bool jacobi_svd_block(fastpi_ctx* h, float* K, float* V, int n, double* sig, int32_t* perm, JacobiStats* stats);
+struct CoreTiling;
+bool jacobi_svd_block(fastpi_ctx* h, float* K, float* V, int n, double* sig, int32_t* perm, JacobiStats* stats,
+                      const CoreTiling* tiling = nullptr, float* ms_out = nullptr, int* sweeps_out = nullptr);
+
+// Tiling of the FP32 core SVD: panel = P (two column blocks of P / 2), parts
+// = CTAs of a cluster sharing a block pair's rows (0: as many as keep one
+// round's clusters on the SMs, at most 8), resident = the resident-block
+// schedule, warp_solve = the P x P Gram sweep by one warp.
+struct CoreTiling {
+  int panel = 16;
+  int parts = 0;
+  bool resident = false;
+  bool warp_solve = true;   // the Gram sweep by one warp (false: by the whole CTA)
+  bool single_cta = false;  // the single-CTA block kernel instead of the cluster form
+  bool strict = false;      // no fallback to the single-CTA kernel when the cluster form does not fit
+};
+// U[:, t] = K[:, perm[t]] / sig[t] (zero when sig[t] = 0), Vs[:, t] = V[:, perm[t]]
+// for the outputs of jacobi_svd_block (n x n column-major, ld n).
+void core_vectors_f32(fastpi_ctx* h, int n, const float* K, const float* V, const double* sig, const int32_t* perm,
+                      float* U, float* Vs);
+// The cluster form of the block Jacobi core SVD (jacobi_cluster.cu): K <- K J
+// and V <- J (n x n, column-major, ld n) as jacobi_svd_block computes them,
+// before the final sort.  false, having done nothing, when the tiling does not
+// fit (shared memory, co-resident clusters) or the launch form is refused.
+bool jacobi_svd_cluster(fastpi_ctx* h, float* K, float* V, int n, const CoreTiling& tiling, JacobiStats* stats,
+                        float* ms, int* sweeps, bool* used_res);
 
 }  // namespace fastpi

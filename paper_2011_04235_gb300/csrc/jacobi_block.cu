@@ -34,225 +34,21 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <string>
 
 #include "jacobi.cuh"
+#include "jacobi_dev.cuh"
+#include "tuning.cuh"
 
 namespace fastpi {
 namespace {
+
+using namespace jdev;
 
 constexpr int BT = 512;              // threads per CTA (16 warps)
 constexpr int B_MAX_SWEEPS = 30;
 constexpr int INNER_SWEEPS = 1;      // sweeps of the P x P Gram solve per block pair
 constexpr float B_EARLY_OFF = 1e-3f;
-constexpr unsigned long long B_WAIT_NS = 2000000000ull;   // bound of every wait (2 s)
-constexpr int VER_STRIDE = 32;   // one 128-byte line per block's round counter (no shared polling lines)
-
-struct BBar {
-  unsigned count;
-  unsigned gen;
-  int flag[3];
-  double fro2;
-};
-
-__device__ __forceinline__ unsigned long long b_gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ unsigned b_ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void b_st_release(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Device-wide barrier of a cooperative launch; false when the bounded wait
-// ran out (status bit set).
-__device__ bool b_barrier(BBar* gb, unsigned* status) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned gen = b_ld_acquire(&gb->gen);
-    __threadfence();
-    const unsigned arrived = atomicAdd(&gb->count, 1u) + 1u;
-    int ok = 1;
-    if (arrived == gridDim.x) {
-      gb->count = 0;
-      __threadfence();
-      b_st_release(&gb->gen, gen + 1u);
-    } else {
-      const unsigned long long t0 = b_gtimer();
-      unsigned spins = 0;
-      while (b_ld_acquire(&gb->gen) == gen) {
-        if ((++spins & 63u) == 0 && b_gtimer() - t0 > B_WAIT_NS) {
-          atomicOr(status, ST_BARRIER_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-__device__ __forceinline__ void circle_pair(int slot, int rr, int qe, int& i, int& j) {
-  const int m = qe - 1;
-  if (slot == 0) {
-    i = m;
-    j = rr;
-  } else {
-    i = rr + slot;
-    if (i >= m) i -= m;
-    j = rr - slot;
-    if (j < 0) j += m;
-  }
-  if (i > j) {
-    const int t = i;
-    i = j;
-    j = t;
-  }
-}
-
-// Partner of column i in round rr of the circle method over qe columns.
-__device__ __forceinline__ int circle_mate(int i, int rr, int qe) {
-  const int m = qe - 1;
-  if (i == m) return rr;
-  if (i == rr) return m;
-  int j = 2 * rr - i;
-  if (j < 0) j += m;
-  if (j >= m) j -= m;
-  return j;
-}
-
-// Butterfly reduction of NV per-lane values over the 32 lanes of a warp.
-// NV >= 32: afterwards lane L holds the sums of values [off, off + NV / 32),
-// off built from the lane bits.  NV < 32: lanes that differ only in their
-// lowest log2(32 / NV) bits hold the same single sum, index off.
-template <int NV>
-__device__ __forceinline__ void warp_reduce_scatter(float (&v)[NV], int lane, int& off) {
-  off = 0;
-  int len = NV;
-#pragma unroll
-  for (int m = 16; m >= 1; m >>= 1) {
-    if (len > 1) {
-      const int half = len / 2;
-      const bool up = (lane & m) != 0;
-#pragma unroll
-      for (int i = 0; i < NV / 2; ++i) {
-        if (i < half) {
-          const float mine = up ? v[i + half] : v[i];
-          const float other = up ? v[i] : v[i + half];
-          v[i] = mine + __shfl_xor_sync(0xffffffffu, other, m);
-        }
-      }
-      if (up) off += half;
-      len = half;
-    } else {
-      v[0] += __shfl_xor_sync(0xffffffffu, v[0], m);
-    }
-  }
-}
-
-__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
-               "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Whole CTA, any P: G and Q in shared memory, double-buffered.  Per round,
-// threads 0..P/2-1 compute the rotations of the round's pairs, then all
-// threads update the P x P entries of G <- J^T G J and Q <- Q J.  Returns
-// the buffer that holds the final Q.  Runs `sweeps` sweeps.
-// Pairs of one inner round.  Full rounds (cross = false): the circle method
-// over all P columns, P - 1 rounds.  Cross rounds (cross = true): column i of
-// the first block with column B + (i + ir) mod B of the second, B rounds.
-template <int P>
-__device__ __forceinline__ void inner_pair(bool cross, int k, int ir, int& p, int& q) {
-  constexpr int B = P / 2;
-  if (cross) {
-    p = k;
-    q = B + (k + ir) % B;
-  } else {
-    circle_pair(k, ir, P, p, q);
-  }
-}
-template <int P>
-__device__ __forceinline__ int inner_mate(bool cross, int i, int ir) {
-  constexpr int B = P / 2;
-  if (!cross) return circle_mate(i, ir, P);
-  return i < B ? B + (i + ir) % B : ((i - B - ir) % B + B) % B;
-}
-
-// Whole CTA, any P: G and Q in shared memory, double-buffered.  Per round,
-// threads 0..P/2-1 compute the rotations of the round's pairs, then all
-// threads update the P x P entries of G <- J^T G J and Q <- Q J.  Returns
-// the buffer that holds the final Q.  `cross`: only the pairs across the two
-// blocks (the pairs inside each block were visited in the first round of
-// the sweep).
-template <int P>
-__device__ __forceinline__ float* inner_solve_cta(float* G, float* Gn, float* Q, float* Qn, float* sc, float* so,
-                                                  int tid, float tabs, float tol2, float early2, int sweeps,
-                                                  bool cross, int* s_rot, int* s_pair_rot) {
-  constexpr int GS = P;
-  const int rounds = cross ? P / 2 : P - 1;
-  for (int is = 0; is < sweeps; ++is) {
-    for (int ir = 0; ir < rounds; ++ir) {
-      if (tid < P / 2) {
-        int p, q;
-        inner_pair<P>(cross, tid, ir, p, q);
-        const float al = G[p * GS + p], be = G[q * GS + q], ga = G[p * GS + q];
-        float c = 1.f, s = 0.f;
-        if (al > tabs && be > tabs && ga * ga > tol2 * al * be) {
-          // t = 2 g sgn(d) / (|d| + sqrt(d^2 + 4 g^2)), d = be - al (smaller root)
-          const float d = be - al;
-          // IEEE square root and division: an approximate c (c^2 + s^2 != 1 by a
-          // few ulp with a fixed sign) would scale V's columns a little on every
-          // one of the thousands of rotations each column receives
-          const float t = 2.f * (d < 0.f ? -ga : ga) / (fabsf(d) + sqrtf(fmaf(d, d, 4.f * ga * ga)));
-          c = 1.f / sqrtf(fmaf(t, t, 1.f));
-          s = c * t;
-          *s_pair_rot = 1;
-          atomicMax(s_rot, ga * ga > early2 * al * be ? 2 : 1);
-        }
-        // x_p' = c x_p - s x_q, x_q' = s x_p + c x_q
-        sc[p] = c;
-        so[p] = -s;
-        sc[q] = c;
-        so[q] = s;
-      }
-      __syncthreads();
-      for (int e = tid; e < P * P; e += BT) {
-        const int i = e / P, j = e % P;
-        const int mi = inner_mate<P>(cross, i, ir), mj = inner_mate<P>(cross, j, ir);
-        const float ci = sc[i], si = so[i], cj = sc[j], sj = so[j];
-        Gn[i * GS + j] = ci * (cj * G[i * GS + j] + sj * G[i * GS + mj]) +
-                         si * (cj * G[mi * GS + j] + sj * G[mi * GS + mj]);
-        Qn[i * GS + j] = cj * Q[i * GS + j] + sj * Q[i * GS + mj];
-      }
-      __syncthreads();
-      float* t = G;
-      G = Gn;
-      Gn = t;
-      t = Q;
-      Q = Qn;
-      Qn = t;
-    }
-  }
-  return Q;
-}
-
 #ifdef FASTPI_PHASE_CLOCKS
 __device__ long long g_phase_clk[8];
 #define PHASE_MARK(k)                          \
@@ -450,7 +246,7 @@ __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
       // inside the blocks in the first round of a sweep (every block meets its
       // first partner there), only cross pairs afterwards, so every column
       // pair is still visited at least once per sweep
-      const float* Qf = inner_solve_cta<P>(G, Gn, Q, Qn, s_sc, s_so, tid, tabs, tol2, early2, a.inner, rr != 0,
+      const float* Qf = inner_solve_cta<P, BT>(G, Gn, Q, Qn, s_sc, s_so, tid, tabs, tol2, early2, a.inner, rr != 0,
                                            &s_rot, &s_pair_rot);
       PHASE_MARK(2);
       cp_async_wait<0>();
@@ -667,12 +463,7 @@ bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats,
   DArr<int> out(2, st);
   DArr<unsigned> ver(int64_t(nb) * VER_STRIDE, st);
   DArr<float> Kp(int64_t(ldk) * n, st), Vp(int64_t(ldk) * n, st);
-  k_b_sumsq_part<<<NPART, 256, 0, st>>>(K, int64_t(n) * n, part.get());
-  CK_LAUNCH();
-  k_b_sumsq_final<<<1, 32, 0, st>>>(part.get(), NPART, gb.get());
-  CK_LAUNCH();
-  k_b_pad_in<<<unsigned((int64_t(ldk) * n + 255) / 256), 256, 0, st>>>(K, n, ldk, Kp.get(), Vp.get());
-  CK_LAUNCH();
+  core_prepare(hc, K, n, ldk, Kp.get(), Vp.get(), part.get(), NPART, gb.get());
   CK(cudaMemsetAsync(out.get(), 0, 2 * sizeof(int), st));
   CK(cudaMemsetAsync(ver.get(), 0, size_t(nb) * VER_STRIDE * sizeof(unsigned), st));
   CK(cudaMemsetAsync(hc->dstatus.get(), 0, 4, st));
@@ -697,8 +488,7 @@ bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats,
   CK(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(BT), args, smem, st));
   CK_LAUNCH();
   CK(cudaEventRecord(ev1, st));
-  k_b_pad_out<<<unsigned((int64_t(n) * n + 255) / 256), 256, 0, st>>>(Kp.get(), Vp.get(), n, ldk, K, V);
-  CK_LAUNCH();
+  core_finish(hc, Kp.get(), Vp.get(), n, ldk, K, V);
   int ho[2] = {0, 0};
   d2h_sync(ho, out.get(), sizeof ho, st);
   unsigned stat = 0;
@@ -734,23 +524,96 @@ bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats,
 
 }  // namespace
 
-bool jacobi_svd_block(fastpi_ctx* hc, float* K, float* V, int n, double* sig, int32_t* perm, JacobiStats* stats) {
+namespace jdev {
+
+void core_prepare(fastpi_ctx* hc, const float* K, int n, int ldk, float* Kp, float* Vp, double* part, int npart,
+                  BBar* gb) {
+  cudaStream_t st = hc->stream;
+  k_b_sumsq_part<<<npart, 256, 0, st>>>(K, int64_t(n) * n, part);
+  CK_LAUNCH();
+  k_b_sumsq_final<<<1, 32, 0, st>>>(part, npart, gb);
+  CK_LAUNCH();
+  k_b_pad_in<<<unsigned((int64_t(ldk) * n + 255) / 256), 256, 0, st>>>(K, n, ldk, Kp, Vp);
+  CK_LAUNCH();
+}
+
+void core_finish(fastpi_ctx* hc, const float* Kp, const float* Vp, int n, int ldk, float* K, float* V) {
+  k_b_pad_out<<<unsigned((int64_t(n) * n + 255) / 256), 256, 0, hc->stream>>>(Kp, Vp, n, ldk, K, V);
+  CK_LAUNCH();
+}
+
+}  // namespace jdev
+
+// Tiling of the core SVD from the environment (measurement switches):
+// FASTPI_CORE_KERNEL=block selects the single-CTA kernel, FASTPI_CORE_P=16|32
+// the panel, FASTPI_CORE_C=1..8 the CTAs per cluster, FASTPI_CORE_WARP=0 the
+// CTA-wide Gram sweep, FASTPI_JACOBI_RESIDENT=1 the resident-block schedule.
+static bool env_int(const char* name, int* v) {
+  const char* e = std::getenv(name);
+  if (!e || !*e) return false;
+  char* end = nullptr;
+  const long x = std::strtol(e, &end, 10);
+  if (*end) return false;
+  *v = int(x);
+  return true;
+}
+
+bool jacobi_svd_block(fastpi_ctx* hc, float* K, float* V, int n, double* sig, int32_t* perm, JacobiStats* stats,
+                      const CoreTiling* tiling, float* ms_out, int* sweeps_out) {
   if (n < 2) return false;
   float ms = 0;
   int sweeps = 0;
-  // blocks of 8 columns (16-column panels) with K and V staged; for wider
-  // cores (n > ~1 790) only K staged, V streamed from L2 (up to n ~ 2 430:
-  // 152 block pairs per round)
   bool res = false;
-  bool ok = launch_block<16, true>(hc, K, V, n, stats, &ms, &sweeps, &res);
-  if (!ok) ok = launch_block<16, false>(hc, K, V, n, stats, &ms, &sweeps, &res);
+  bool ok = false;
+  CoreTiling tl;
+  if (tiling) {
+    tl = *tiling;
+  } else {
+    tuned_core_tiling(n, &tl);
+    const char* kind = std::getenv("FASTPI_CORE_KERNEL");
+    tl.single_cta = kind && std::string(kind) == "block";
+    int v = 0;
+    if (env_int("FASTPI_CORE_P", &v) && (v == 16 || v == 32)) tl.panel = v;
+    if (env_int("FASTPI_CORE_C", &v) && v >= 1 && v <= 8) tl.parts = v;
+    if (env_int("FASTPI_CORE_WARP", &v)) tl.warp_solve = v != 0;
+    if (std::getenv("FASTPI_JACOBI_RESIDENT")) tl.resident = resident_schedule();
+  }
+  if (!tl.single_cta) ok = jacobi_svd_cluster(hc, K, V, n, tl, stats, &ms, &sweeps, &res);
+  if (!ok && !(tl.strict && !tl.single_cta)) {
+    // the single-CTA kernel (its resident form from the environment only)
+    ok = launch_block<16, true>(hc, K, V, n, stats, &ms, &sweeps, &res);
+    if (!ok) ok = launch_block<16, false>(hc, K, V, n, stats, &ms, &sweeps, &res);
+  }
   if (!ok) return false;
+  if (ms_out) *ms_out = ms;
+  if (sweeps_out) *sweeps_out = sweeps;
   std::vector<JacobiProblem<float>> pr(1);
   pr[0] = JacobiProblem<float>{K, V, n, n, n, n};
   jacobi_sort_columns<float>(hc, pr, sig, perm);
   const double dn = n;
   note_svd(SVD_CORE32, ms, 12 * dn * dn * dn, double(sweeps) * (dn * (dn - 1) / 2) * (12 * dn + 6 * dn), res);
   return true;
+}
+
+
+namespace {
+__global__ void k_core_uv(int n, const float* __restrict__ K, const float* __restrict__ V,
+                          const double* __restrict__ sig, const int32_t* __restrict__ perm, float* __restrict__ U,
+                          float* __restrict__ Vs) {
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= int64_t(n) * n) return;
+  const int t = int(e / n), i = int(e % n);
+  const int src = perm[t];
+  const double s = sig[t];
+  U[e] = s > 0 ? float(double(K[int64_t(src) * n + i]) / s) : 0.f;
+  Vs[e] = V[int64_t(src) * n + i];
+}
+}  // namespace
+
+void core_vectors_f32(fastpi_ctx* h, int n, const float* K, const float* V, const double* sig, const int32_t* perm,
+                      float* U, float* Vs) {
+  k_core_uv<<<unsigned((int64_t(n) * n + 255) / 256), 256, 0, h->stream>>>(n, K, V, sig, perm, U, Vs);
+  CK_LAUNCH();
 }
 
 }  // namespace fastpi

@@ -30,7 +30,7 @@ SYMBOLS = ["fastpi_create", "fastpi_create_from_factors", "fastpi_truncate", "fa
            "fastpi_residual", "fastpi_residual_noalloc", "fastpi_spmm", "fastpi_recon_error", "fastpi_get_rank", "fastpi_get_S", "fastpi_get_U",
            "fastpi_get_V",
            "fastpi_get_perm", "fastpi_get_blocks", "fastpi_get_info", "fastpi_get_counters",
-           "fastpi_reset_counters", "fastpi_gemm_f32", "fastpi_last_error", "fastpi_destroy"]
+           "fastpi_reset_counters", "fastpi_gemm_f32", "fastpi_core_svd_f32", "fastpi_load_tuning", "fastpi_last_error", "fastpi_destroy"]
 
 
 class FastPIError(RuntimeError):
@@ -147,6 +147,38 @@ def gemm_f32(A: torch.Tensor, B: torch.Tensor, ta: bool = False, tb: bool = Fals
     return Cout
 
 
+def core_svd_f32(K: torch.Tensor, panel: int = 16, parts: int = 0, resident: bool = False, warp: bool = True,
+                 single_cta: bool = False):
+    """SVD of a square FP32 matrix by the library's core-SVD kernel (block
+    one-sided Jacobi) with the given tiling.  K: n x n CUDA tensor (any float
+    dtype; copied).  Returns (S numpy float64 descending, U, V float32 CUDA
+    tensors with singular vectors as columns, sweeps, kernel ms)."""
+    n = int(K.shape[0])
+    if K.dim() != 2 or K.shape[1] != n or not K.is_cuda:
+        raise ValueError("K must be a square CUDA matrix")
+    Kc = K.to(torch.float32).t().contiguous()           # column-major storage of K
+    U = torch.empty((n, n), dtype=torch.float32, device=K.device)
+    V = torch.empty((n, n), dtype=torch.float32, device=K.device)
+    S = np.empty(n, dtype=np.float64)
+    sw, ms = C.c_int(), C.c_float()
+    flags = (1 if resident else 0) | (0 if warp else 2) | (4 if single_cta else 0)
+    st = torch.cuda.current_stream(K.device).cuda_stream
+    with torch.cuda.device(K.device):
+        _check(lib().fastpi_core_svd_f32(n, _ptr(Kc), _ptr(U), S.ctypes.data, _ptr(V), int(panel), int(parts), flags,
+                                         C.byref(sw), C.byref(ms), st))
+    # column-major results: the singular vectors are the rows of the row-major views
+    return S, U.t(), V.t(), sw.value, ms.value
+
+
+TUNING_PATH = os.path.join(_HERE, "tuning.txt")
+
+
+def load_tuning(path: str | None) -> None:
+    """Replace the library's tuning table with the file at path (None: the
+    built-in defaults)."""
+    _check(lib().fastpi_load_tuning(None if path is None else os.fsencode(path)))
+
+
 def load_library(path: str = LIB_PATH) -> C.CDLL:
     if not os.path.exists(path):
         raise ImportError(f"libfastpi.so not built at {path}; run python -m paper_2011_04235_gb300.build")
@@ -169,6 +201,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fastpi_residual_noalloc": ([i64, i64, vp, vp, vp, vp, i64, i64, vp, i64, C.POINTER(dbl), vp], i32),
         "fastpi_gemm_f32": ([i32, i32, i64, i64, i64, C.c_float, vp, i64, vp, i64, C.c_float, vp, i64, i32, vp],
                             i32),
+        "fastpi_core_svd_f32": ([i32, vp, vp, vp, vp, i32, i32, i32, C.POINTER(i32), C.POINTER(C.c_float), vp],
+                                i32),
+        "fastpi_load_tuning": ([C.c_char_p], i32),
         "fastpi_get_rank": ([p, C.POINTER(i64)], i32),
         "fastpi_get_S": ([p, vp], i32),
         "fastpi_get_U": ([p, vp, i64], i32),

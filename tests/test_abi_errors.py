@@ -91,3 +91,20 @@ def test_batched_and_gemm_and_noalloc_argument_checks(lib):
     assert lib.fastpi_residual_noalloc(1, 1, rp.ctypes.data, None, None, None, 0, 0, None, 0, None, None) == ERR_ARG
     assert lib.fastpi_residual_noalloc((1 << 20) + 1, 1, rp.ctypes.data, None, None, None, 0, 0, None, 0,
                                        C.byref(d), None) == ERR_ARG
+
+
+def test_tuning_table_parsing(lib, tmp_path):
+    """fastpi_load_tuning reads the autotuner's table (no GPU call): a
+    well-formed file loads, a malformed line or a missing file is refused with
+    FASTPI_ERR_ARG and a message, and NULL restores the built-in defaults."""
+    good = tmp_path / "t.txt"
+    good.write_text("# comment\ncore 600 16 4 0 1\ncore 1048576 32 8 1 1\nchunk 1 0 491 320\n"
+                    "chunk 0 1 1099511627776 256\nbucket 1 256 1\n")
+    assert lib.fastpi_load_tuning(str(good).encode()) == 0
+    for bad in ("core 600 24 4 0 1\n", "chunk 2 0 10 256\n", "bucket 1 256 9\n", "core 600 16\n", "foo 1\n"):
+        p = tmp_path / "bad.txt"
+        p.write_text(bad)
+        assert lib.fastpi_load_tuning(str(p).encode()) == ERR_ARG
+        assert lib.fastpi_last_error(None)
+    assert lib.fastpi_load_tuning(str(tmp_path / "missing.txt").encode()) == ERR_ARG
+    assert lib.fastpi_load_tuning(None) == 0
