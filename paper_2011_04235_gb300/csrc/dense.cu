@@ -7,6 +7,8 @@
 // has too few tiles to fill the 152 SMs the K dimension is split across CTAs
 // and the partial tiles are summed afterwards in a fixed order (so results do
 // not depend on scheduling).
+#include <algorithm>
+
 #include "dense.cuh"
 
 namespace fastpi {
@@ -137,6 +139,86 @@ __global__ void k_set(int64_t rows, int64_t cols, T* a, int64_t ld, int ident) {
   a[i * ld + j] = (ident && i == j) ? T(1) : T(0);
 }
 
+// Gram matrix G = X^T X (c x c, FP64) of an FP32 matrix X (p x c, row-major,
+// ld) on the FP32 pipe with about 48 significand bits: every product is split
+// exactly (x y = h + e with h = rn(x y) and e = fma(x, y, -h)), the sum of the
+// h is carried as an unevaluated pair hi + lo (TwoSum: the rounding error of
+// each addition goes to lo) and the e are added to lo.  Explicitly rounded
+// operations keep the compiler from fusing a product into an addition, which
+// would break the error terms.  Only the 64 x 64 tiles on or above the
+// diagonal are formed (blockIdx.x enumerates them), each written with its
+// mirror; K is split over blockIdx.z into partial tiles W[z] (c x c) that a
+// fixed-order reduction sums.
+constexpr int GTILE = 64;
+__global__ void __launch_bounds__(NT) k_gram_ff(int64_t p, int c, const float* __restrict__ X, int64_t ld,
+                                                int64_t kchunk, double* __restrict__ W) {
+  __shared__ float As[BK][GTILE + 1];
+  __shared__ float Bs[BK][GTILE + 1];
+  const int nt = (c + GTILE - 1) / GTILE;
+  int idx = int(blockIdx.x), ti = 0;
+  while (idx >= nt - ti) {
+    idx -= nt - ti;
+    ++ti;
+  }
+  const int tj = ti + idx;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = ti * GTILE, j0 = tj * GTILE;
+  const int64_t k_begin = int64_t(blockIdx.z) * kchunk;
+  const int64_t k_end = (k_begin + kchunk < p) ? k_begin + kchunk : p;
+  float hi[4][4], lo[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) hi[i][j] = lo[i][j] = 0.f;
+  for (int64_t k0 = k_begin; k0 < k_end; k0 += BK) {
+#pragma unroll
+    for (int e = 0; e < (GTILE * BK) / NT; ++e) {
+      const int lin = tid + NT * e;
+      const int kk = lin / GTILE, i = lin % GTILE;
+      const int64_t gk = k0 + kk;
+      const bool krow = gk < k_end;
+      As[kk][i] = (krow && i0 + i < c) ? X[gk * ld + i0 + i] : 0.f;
+      Bs[kk][i] = (krow && j0 + i < c) ? X[gk * ld + j0 + i] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float h = __fmul_rn(a[i], b[j]);
+          const float e = fmaf(a[i], b[j], -h);
+          const float s = __fadd_rn(hi[i][j], h);
+          const float bb = __fsub_rn(s, hi[i][j]);
+          const float err = __fadd_rn(__fsub_rn(hi[i][j], __fsub_rn(s, bb)), __fsub_rn(h, bb));
+          hi[i][j] = s;
+          lo[i][j] = __fadd_rn(lo[i][j], __fadd_rn(err, e));
+        }
+    }
+    __syncthreads();
+  }
+  double* Wz = W + int64_t(blockIdx.z) * c * c;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gi = i0 + ty + 16 * i;
+    if (gi >= c) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gj = j0 + tx + 16 * j;
+      if (gj >= c) continue;
+      const double v = double(hi[i][j]) + double(lo[i][j]);
+      Wz[int64_t(gi) * c + gj] = v;
+      Wz[int64_t(gj) * c + gi] = v;
+    }
+  }
+}
+
 int g_num_sms = 0;
 int num_sms() {
   if (!g_num_sms) {
@@ -211,6 +293,31 @@ void gemm_f32(cudaStream_t st, bool ta, bool tb, int64_t M, int64_t N, int64_t K
     gemm_tf32(st, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 3);
   else
     gemm<float>(st, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+void gram_ff(cudaStream_t st, int64_t p, int64_t c, const float* X, int64_t ld, double* G) {
+  if (c <= 0) return;
+  if (p <= 0) {
+    set_zero<double>(st, c, c, G, c);
+    return;
+  }
+  const int64_t nt = (c + GTILE - 1) / GTILE, tiles = nt * (nt + 1) / 2;
+  if (tiles > 65535) fail(FASTPI_ERR_ARG, "gram: too many columns");
+  const int64_t target = 2 * int64_t(num_sms());
+  int64_t splits = std::max<int64_t>(1, (target + tiles - 1) / tiles);
+  splits = std::min<int64_t>(splits, std::max<int64_t>(1, p / (BK * 8)));
+  splits = std::min<int64_t>(splits, 128);
+  int64_t kchunk = (p + splits - 1) / splits;
+  kchunk = (kchunk + BK - 1) / BK * BK;
+  splits = (p + kchunk - 1) / kchunk;
+  DArr<double> work(splits > 1 ? splits * c * c : 1, st);
+  double* W = splits > 1 ? work.get() : G;
+  k_gram_ff<<<dim3(unsigned(tiles), 1, unsigned(splits)), NT, 0, st>>>(p, int(c), X, ld, kchunk, W);
+  CK_LAUNCH();
+  if (splits > 1) {
+    k_splitk_reduce<double><<<grid1(c * c), 256, 0, st>>>(c, c, int(splits), W, 0.0, G, c);
+    CK_LAUNCH();
+  }
 }
 
 template void gemm_mixed<float, double>(cudaStream_t, bool, bool, int64_t, int64_t, int64_t, double, const float*,

@@ -20,6 +20,11 @@ template <typename TI, typename T>
 void gemm_mixed(cudaStream_t st, bool ta, bool tb, int64_t M, int64_t N, int64_t K, T alpha, const TI* A,
                 int64_t lda, const TI* B, int64_t ldb, T beta, T* C, int64_t ldc);
 
+// G (c x c, FP64, row-major) = X^T X for X (p x c, FP32, row-major, ld): the
+// products split exactly and summed as FP32 pairs (about 48 significand bits)
+// on the FP32 pipe; symmetric tiles formed once.
+void gram_ff(cudaStream_t st, int64_t p, int64_t c, const float* X, int64_t ld, double* G);
+
 // Same contract with FP32 storage on the TF32 tensor cores (tcgen05.mma,
 // kind::tf32, FP32 accumulation in tensor memory, TMA-staged operands).
 // passes = 1: operands rounded to TF32; passes = 3: split hi + lo TF32

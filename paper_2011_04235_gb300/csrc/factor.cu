@@ -712,14 +712,14 @@ struct Phase {
     DArr<double> G(c * c, st), Linv(c * c, st), G2(c * c, st), L2inv(c * c, st), M(c * c, st);
     DArr<double> Lo(c * c, st), Lp(c * c, st), X(c * c, st);
     DArr<int32_t> kept(c, st), kept2(c, st), piv(c, st), rk(2, st);
-    // FP64 Gram of the residual: in the mixed mode from FP32 data with FP64
-    // accumulation (the products are exact), so that its rounding floor sits
-    // far below the drop tolerance
+    // FP64 Gram of the residual: in the mixed mode from FP32 data, each
+    // product split exactly and summed in FP32 pairs (about 48 bits), so that
+    // its rounding floor sits far below the drop tolerance
     auto gram = [&](const T* X, double* Gd) {
       if constexpr (sizeof(T) == 8)
         gemm<double>(st, true, false, c, c, p, 1.0, X, c, X, c, 0.0, Gd, c);
       else
-        gemm_mixed<float, double>(st, true, false, c, c, p, 1.0, X, c, X, c, 0.0, Gd, c);
+        gram_ff(st, p, c, X, c, Gd);
     };
     auto trinv = [&](auto* L, const int32_t* kp, auto* Xo) {
       using E = std::remove_pointer_t<decltype(L)>;
