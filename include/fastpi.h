@@ -327,7 +327,8 @@ fastpi_status fastpi_gemm_f32(int ta, int tb, int64_t M, int64_t N, int64_t K, f
  * or 32 columns per block pair, parts = CTAs of a thread-block cluster that
  * share a block pair's rows (1..8; 0 picks the largest that keeps one round's
  * clusters on the SMs); flags: 1 = resident-block schedule, 2 = the Gram
- * sweep by the whole CTA instead of one warp, 4 = the single-CTA kernel
+ * sweep in its IEEE form (two CTA barriers per inner round) instead of the
+ * fast one (one barrier, fast rotations), 4 = the single-CTA kernel
  * (panel 16, no clusters).  *sweeps and *ms (may be NULL) receive the sweeps
  * and the CUDA-event time of the Jacobi kernel.  Errors: FASTPI_ERR_ARG
  * (sizes, flags, or a tiling that does not fit: shared memory or co-resident
@@ -339,7 +340,7 @@ fastpi_status fastpi_core_svd_f32(int n, float* K, float* U, double* S, float* V
 /* Tuning table (no citation: parameters of this implementation, picked on the
  * GPU by the package's autotuner, python -m paper_2011_04235_gb300.autotune).
  * A plain-text file of lines
- *   core   <n_max> <panel> <parts> <resident> <warp>   FP32 core-SVD tiling for n <= n_max
+ *   core   <n_max> <panel> <parts> <resident> <fast>   FP32 core-SVD tiling for n <= n_max
  *   chunk  <prec> <phase> <k_max> <c>                  appends of c border rows (phase 0) /
  *                                                      columns (phase 1) when fastpi_factor
  *                                                      gets chunk 0; prec 0 FP64, 1 mixed

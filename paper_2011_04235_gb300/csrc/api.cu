@@ -473,7 +473,7 @@ fastpi_status fastpi_core_svd_f32(int n, float* K, float* U, double* S, float* V
     tl.panel = panel;
     tl.parts = parts;
     tl.resident = (flags & 1) != 0;
-    tl.warp_solve = (flags & 2) == 0;
+    tl.fast_solve = (flags & 2) == 0;
     tl.single_cta = (flags & 4) != 0;
     tl.strict = true;
     DArr<float> J(int64_t(n) * n, ctx.stream);

@@ -47,12 +47,13 @@ bool jacobi_svd_block(fastpi_ctx* h, float* K, float* V, int n, double* sig, int
 // Tiling of the FP32 core SVD: panel = P (two column blocks of P / 2), parts
 // = CTAs of a cluster sharing a block pair's rows (0: as many as keep one
 // round's clusters on the SMs, at most 8), resident = the resident-block
-// schedule, warp_solve = the P x P Gram sweep by one warp.
+// schedule, fast_solve = the P x P Gram sweep with one CTA barrier per inner
+// round and fast rotations (false: two barriers and IEEE rotations).
 struct CoreTiling {
   int panel = 16;
   int parts = 0;
   bool resident = false;
-  bool warp_solve = true;   // the Gram sweep by one warp (false: by the whole CTA)
+  bool fast_solve = true;   // the Gram sweep with one barrier per inner round and fast rotations
   bool single_cta = false;  // the single-CTA block kernel instead of the cluster form
   bool strict = false;      // no fallback to the single-CTA kernel when the cluster form does not fit
 };

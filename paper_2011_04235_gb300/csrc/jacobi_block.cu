@@ -247,7 +247,9 @@ __global__ void __launch_bounds__(BT, 1) k_jacobi_block(BlkArgs a) {
       // first partner there), only cross pairs afterwards, so every column
       // pair is still visited at least once per sweep
       const float* Qf = inner_solve_cta<P, BT>(G, Gn, Q, Qn, s_sc, s_so, tid, tabs, tol2, early2, a.inner, rr != 0,
-                                           &s_rot, &s_pair_rot);
+                                               &s_rot, &s_pair_rot);
+      // Q orthonormal to rounding (no drift of the FP32 rotations; G and Gn are free now)
+      if (s_pair_rot) Qf = ns_orthonormalize<P, BT>(Qf, Gn, Qf == Q ? Qn : Q, tid);
       PHASE_MARK(2);
       cp_async_wait<0>();
       __syncthreads();
@@ -546,8 +548,8 @@ void core_finish(fastpi_ctx* hc, const float* Kp, const float* Vp, int n, int ld
 
 // Tiling of the core SVD from the environment (measurement switches):
 // FASTPI_CORE_KERNEL=block selects the single-CTA kernel, FASTPI_CORE_P=16|32
-// the panel, FASTPI_CORE_C=1..8 the CTAs per cluster, FASTPI_CORE_WARP=0 the
-// CTA-wide Gram sweep, FASTPI_JACOBI_RESIDENT=1 the resident-block schedule.
+// the panel, FASTPI_CORE_C=1..8 the CTAs per cluster, FASTPI_CORE_FAST=0 the
+// IEEE Gram sweep, FASTPI_JACOBI_RESIDENT=1 the resident-block schedule.
 static bool env_int(const char* name, int* v) {
   const char* e = std::getenv(name);
   if (!e || !*e) return false;
@@ -575,7 +577,7 @@ bool jacobi_svd_block(fastpi_ctx* hc, float* K, float* V, int n, double* sig, in
     int v = 0;
     if (env_int("FASTPI_CORE_P", &v) && (v == 16 || v == 32)) tl.panel = v;
     if (env_int("FASTPI_CORE_C", &v) && v >= 1 && v <= 8) tl.parts = v;
-    if (env_int("FASTPI_CORE_WARP", &v)) tl.warp_solve = v != 0;
+    if (env_int("FASTPI_CORE_FAST", &v)) tl.fast_solve = v != 0;
     if (std::getenv("FASTPI_JACOBI_RESIDENT")) tl.resident = resident_schedule();
   }
   if (!tl.single_cta) ok = jacobi_svd_cluster(hc, K, V, n, tl, stats, &ms, &sweeps, &res);

@@ -11,15 +11,17 @@
 //      (per-(block, part) release / acquire round counters, bounded waits);
 //   2. copies its rows of the K panel (and, overlapped, of the V panel) into
 //      shared memory with 16-byte asynchronous copies;
-//   3. forms its partial Gram matrix (P x P) and leaves it in its shared
-//      memory; one cluster barrier later every CTA sums the C partials in
-//      rank order through distributed shared memory, so all C CTAs hold the
-//      same Gram matrix bit for bit;
-//   4. runs the same Jacobi sweep on it (the same rotations in every CTA) and
+//   3. forms its partial Gram matrix (P x P) and stores it into the shared
+//      memory of every CTA of the cluster (distributed shared memory); one
+//      cluster barrier later every CTA sums the C partials in rank order from
+//      its own shared memory, so all C CTAs hold the same Gram matrix bit for
+//      bit;
+//   4. runs the same Jacobi sweep on it (the same rotations in every CTA),
+//      takes one Newton-Schulz step on the accumulated rotation Q (so that it
+//      is orthonormal to rounding, without the drift of FP32 rotations) and
 //      applies Q to its own rows.
 // Load, Gram and update shrink by C per CTA and C times more SMs work; the
-// price is one cluster barrier and C distributed-shared-memory reads per
-// Gram entry per round.
+// price is one cluster barrier and C remote stores per Gram entry per round.
 //
 // Cluster barriers cannot time out, so every CTA of a cluster executes the
 // same sequence of them on every path: one per round, two at the end of each
@@ -77,7 +79,7 @@ __device__ long long g_cphase_clk[8];
   } while (0)
 #endif
 
-template <int P, bool RES, bool WS>
+template <int P, bool RES, bool FAST>
 __global__ void __launch_bounds__(CT) k_jacobi_cluster(ClArgs a) {
   constexpr int B = P / 2;    // columns per block
   constexpr int TW = P / 4;   // Gram tile edge (4 x 4 tiles of TW x TW)
@@ -102,8 +104,9 @@ __global__ void __launch_bounds__(CT) k_jacobi_cluster(ClArgs a) {
   float* Q = G + PP;
   float* Gn = Q + PP;
   float* Qn = Gn + PP;
-  float* Gp = Qn + PP;                           // [2][P][P]: partial Gram, by round parity
-  __shared__ int s_hdr[2];                       // failure flag of this CTA, by round parity
+  float* Rx = Qn + PP;                           // [2][C][P][P]: the partial Grams of the cluster's CTAs,
+                                                 // pushed here by their owners, by round parity
+  __shared__ int s_hdr[2][8];                    // failure flags of the cluster's CTAs, by round parity
   __shared__ int s_dec;                          // stop decision at the end of a sweep
   __shared__ float s_sc[P], s_so[P];
   __shared__ int s_gcol[P];
@@ -206,8 +209,10 @@ __global__ void __launch_bounds__(CT) k_jacobi_cluster(ClArgs a) {
         __syncthreads();
         CPHASE_MARK(0);
         // 3. partial Gram of this part's rows: warp w owns tiles w, w + 8 of
-        // the 4 x 4 tiles; lanes split the rows
-        float* gp = Gp + buf * PP;
+        // the 4 x 4 tiles; lanes split the rows.  Each sum is stored straight
+        // into slot `part` of every CTA of the cluster (this one included),
+        // so that after the barrier each CTA reads only its own shared memory
+        float* gp = Rx + (size_t(buf) * C + part) * PP;
         for (int tile = warp; tile < 16; tile += CT / 32) {
           const int tp = tile >> 2, tq = tile & 3;
           float acc[TW * TW];
@@ -234,47 +239,53 @@ __global__ void __launch_bounds__(CT) k_jacobi_cluster(ClArgs a) {
 #pragma unroll
             for (int e = 0; e < ((TW * TW) >= 32 ? (TW * TW) / 32 : 1); ++e) {
               const int idx = off + e, i = idx / TW, j = idx % TW;
-              gp[(tp * TW + i) * P + tq * TW + j] = acc[e];
+              for (int c = 0; c < C; ++c) cl.map_shared_rank(gp, c)[(tp * TW + i) * P + tq * TW + j] = acc[e];
             }
           } else if ((lane & (32 / (TW * TW) - 1)) == 0) {
             const int i = off / TW, j = off % TW;
-            gp[(tp * TW + i) * P + tq * TW + j] = acc[0];
+            for (int c = 0; c < C; ++c) cl.map_shared_rank(gp, c)[(tp * TW + i) * P + tq * TW + j] = acc[0];
           }
         }
       }
-      if (tid == 0) s_hdr[buf] = ok ? 0 : 1;
+      if (tid < C) cl.map_shared_rank(&s_hdr[buf][0], tid)[part] = ok ? 0 : 1;
       CPHASE_MARK(1);
-      // the exchange: every CTA of the cluster has left its partial Gram and
-      // its flag in its shared memory
+      // the exchange: every CTA of the cluster has pushed its partial Gram and
+      // its flag into every CTA's shared memory
       cl.sync();
       CPHASE_MARK(7);
       int anyerr = 0;
-      for (int c = 0; c < C; ++c) anyerr |= cl.map_shared_rank(s_hdr, c)[buf];
+      for (int c = 0; c < C; ++c) anyerr |= s_hdr[buf][c];
       if (anyerr) {
-        // leave together; nobody reads a peer's shared memory after this barrier
+        // leave together; nobody touches a peer's shared memory after this barrier
         cp_async_wait<0>();
         __syncthreads();
         cl.sync();
         return;
       }
-      for (int e = tid; e < PP; e += CT) {
-        float s = 0.f;
-        for (int c = 0; c < C; ++c) s += cl.map_shared_rank(Gp, c)[buf * PP + e];
-        G[e] = s;
-        Q[e] = (e / P == e % P) ? 1.f : 0.f;
+      {
+        const float* rx = Rx + size_t(buf) * C * PP;
+        for (int e = tid; e < PP; e += CT) {
+          float sum = 0.f;
+          for (int c = 0; c < C; ++c) sum += rx[size_t(c) * PP + e];
+          G[e] = sum;
+          Q[e] = (e / P == e % P) ? 1.f : 0.f;
+        }
       }
       __syncthreads();
       CPHASE_MARK(2);
-      // 4. the Jacobi sweep on G (identical in every CTA of the cluster): one
-      // warp, or the whole CTA
-      const float* Qf = Q;
-      if (WS) {
-        if (warp == 0) inner_solve_warp<P>(G, Q, s_sc, s_so, lane, tabs, tol2, early2, rr != 0, &s_rot, &s_pair_rot);
+      // 4. the Jacobi sweep on G (identical in every CTA of the cluster): with
+      // one barrier per inner round and fast rotations, or the IEEE form with
+      // two barriers per inner round
+      float* Qf = Q;
+      if (FAST) {
+        inner_solve_fast<P, CT>(G, Gn, Q, tid, tabs, tol2, early2, rr != 0, &s_rot, &s_pair_rot);
         __syncthreads();
       } else {
         Qf = inner_solve_cta<P, CT>(G, Gn, Q, Qn, s_sc, s_so, tid, tabs, tol2, early2, 1, rr != 0, &s_rot,
                                     &s_pair_rot);
       }
+      // Q orthonormal to rounding (G and Gn are free now)
+      if (s_pair_rot) Qf = ns_orthonormalize<P, CT>(Qf, Gn, Qf == Q ? Qn : Q, tid);
       CPHASE_MARK(3);
       cp_async_wait<0>();
       __syncthreads();
@@ -392,8 +403,8 @@ __global__ void __launch_bounds__(CT) k_jacobi_cluster(ClArgs a) {
   }
 }
 
-size_t cluster_smem(int P, int rpc) {
-  return (2 * size_t(P) * rpc + 6 * size_t(P) * P) * sizeof(float);
+size_t cluster_smem(int P, int C, int rpc) {
+  return (2 * size_t(P) * rpc + (4 + 2 * size_t(C)) * size_t(P) * P) * sizeof(float);
 }
 
 // C (CTAs per cluster) for an n-column core: as many row parts as keep the
@@ -405,7 +416,7 @@ int pick_parts(int slots, int num_sms, int want) {
   return std::max(1, std::min(8, c));
 }
 
-template <int P, bool RES, bool WS>
+template <int P, bool RES, bool FAST>
 bool launch_cluster(fastpi_ctx* hc, float* K, float* V, int n, int parts, JacobiStats* stats, float* ms_out,
                     int* sweeps) {
   cudaStream_t st = hc->stream;
@@ -418,11 +429,11 @@ bool launch_cluster(fastpi_ctx* hc, float* K, float* V, int n, int parts, Jacobi
   int rpc = (n + C - 1) / C;
   rpc = (rpc + 3) / 4 * 4;
   const int ldk = C * rpc;
-  const size_t smem = cluster_smem(P, rpc);
+  const size_t smem = cluster_smem(P, C, rpc);
   int max_smem = 0;
   CK(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, hc->device));
   if (smem + 1024 > size_t(max_smem)) return false;
-  const void* kern = (const void*)k_jacobi_cluster<P, RES, WS>;
+  const void* kern = (const void*)k_jacobi_cluster<P, RES, FAST>;
   allow_max_dynamic_smem(kern);
 
   cudaLaunchConfig_t cfg = {};
@@ -477,7 +488,7 @@ bool launch_cluster(fastpi_ctx* hc, float* K, float* V, int n, int parts, Jacobi
   CK(cudaEventCreate(&ev0));
   CK(cudaEventCreate(&ev1));
   CK(cudaEventRecord(ev0, st));
-  const cudaError_t le = cudaLaunchKernelEx(&cfg, k_jacobi_cluster<P, RES, WS>, a);
+  const cudaError_t le = cudaLaunchKernelEx(&cfg, k_jacobi_cluster<P, RES, FAST>, a);
   if (le != cudaSuccess) {
     // not launchable in this form (for example a cooperative cluster launch
     // refused): nothing ran; the caller takes the single-CTA kernel
@@ -533,7 +544,7 @@ bool jacobi_svd_cluster(fastpi_ctx* hc, float* K, float* V, int n, const CoreTil
   const int C = pick_parts(std::max(nb / 2, 1), hc->num_sms, tiling.parts);
   *used_res = tiling.resident;
 #define FASTPI_CL(PV, RV, WV) launch_cluster<PV, RV, WV>(hc, K, V, n, C, stats, ms, sweeps)
-  const bool r = tiling.resident, w = tiling.warp_solve;
+  const bool r = tiling.resident, w = tiling.fast_solve;
   if (P == 16) return r ? (w ? FASTPI_CL(16, true, true) : FASTPI_CL(16, true, false))
                         : (w ? FASTPI_CL(16, false, true) : FASTPI_CL(16, false, false));
   if (P == 32) return r ? (w ? FASTPI_CL(32, true, true) : FASTPI_CL(32, true, false))

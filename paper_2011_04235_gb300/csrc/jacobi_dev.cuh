@@ -221,72 +221,116 @@ __device__ __forceinline__ float* inner_solve_cta(float* G, float* Gn, float* Q,
 }
 
 
-// The same sweep on G by ONE warp (the caller's other warps wait at a CTA
-// barrier afterwards): per inner round the lanes holding a pair compute its
-// rotation, then every lane rotates whole 2 x 2 blocks of G (rows {i, mi},
-// columns {j, mj}) and pairs of entries of Q's rows in place -- a block is
-// read and written by one lane only -- with warp barriers instead of CTA
-// barriers between the steps.  G and Q are P x P row-major in shared memory;
-// sc / so receive the rotation of each column (x_i' = sc_i x_i + so_i
-// x_mate(i)).  On return Q holds the accumulated rotations, *rot_flag the
-// largest rotation class of the sweep (0 none, 1 above tol, 2 above the early
-// exit threshold), *pair_rot whether any pair rotated (lane 0 writes both).
+// Rotation of the pair (p, q) from the Gram entries al = G_pp, be = G_qq,
+// ga = G_pq (row-major P x P): t = 2 g sgn(d) / (|d| + sqrt(d^2 + 4 g^2)),
+// d = be - al (the smaller root), c = 1 / sqrt(1 + t^2), s = c t, with the
+// fast reciprocal square root and division (the caller re-orthonormalises the
+// accumulated rotation, so their last-ulp errors do not accumulate).  cls: 0
+// no rotation, 1 above tol, 2 above the early-exit threshold.
 template <int P>
-__device__ __forceinline__ void inner_solve_warp(float* G, float* Q, float* sc, float* so, int lane, float tabs,
-                                                 float tol2, float early2, bool cross, int* rot_flag,
-                                                 int* pair_rot) {
+__device__ __forceinline__ void rot_fast(const float* G, int p, int q, float tabs, float tol2, float early2, float& c,
+                                         float& s, int& cls) {
+  const float al = G[p * P + p], be = G[q * P + q], ga = G[p * P + q];
+  c = 1.f;
+  s = 0.f;
+  cls = 0;
+  if (al > tabs && be > tabs && ga * ga > tol2 * al * be) {
+    const float d = be - al;
+    const float h = fmaf(d, d, 4.f * ga * ga);
+    const float t = __fdividef(2.f * (d < 0.f ? -ga : ga), fabsf(d) + h * rsqrtf(h));
+    c = rsqrtf(fmaf(t, t, 1.f));
+    s = c * t;
+    cls = ga * ga > early2 * al * be ? 2 : 1;
+  }
+}
+
+// The sweep on G with ONE CTA barrier per inner round: every work item --
+// a 2 x 2 block of G (rows {i, mi}, columns {j, mj}) or a pair of entries of
+// a row of Q -- computes the rotations it needs from the current G itself
+// (the same inputs and code in every thread, so the same values), reads G
+// from one buffer and writes the rotated block to the other, and rotates its
+// entries of Q in place.  Returns the buffer that holds the final G; the
+// largest rotation class goes to *rot_flag and whether any pair rotated to
+// *pair_rot (both through shared-memory atomics).
+template <int P, int NT>
+__device__ __forceinline__ void inner_solve_fast(float* G, float* Gn, float* Q, int tid, float tabs, float tol2,
+                                                 float early2, bool cross, int* rot_flag, int* pair_rot) {
   constexpr int H = P / 2;
+  constexpr int NB = H * H, NQ = P * H;
   const int rounds = cross ? H : P - 1;
   int rot = 0;
   for (int ir = 0; ir < rounds; ++ir) {
-    if (lane < H) {
-      int p, q;
-      inner_pair<P>(cross, lane, ir, p, q);
-      const float al = G[p * P + p], be = G[q * P + q], ga = G[p * P + q];
-      float c = 1.f, s = 0.f;
-      if (al > tabs && be > tabs && ga * ga > tol2 * al * be) {
-        // t = 2 g sgn(d) / (|d| + sqrt(d^2 + 4 g^2)), d = be - al (the smaller
-        // root); IEEE square root and division keep c^2 + s^2 = 1 unbiased
-        const float d = be - al;
-        const float t = 2.f * (d < 0.f ? -ga : ga) / (fabsf(d) + sqrtf(fmaf(d, d, 4.f * ga * ga)));
-        c = 1.f / sqrtf(fmaf(t, t, 1.f));
-        s = c * t;
-        rot = max(rot, ga * ga > early2 * al * be ? 2 : 1);
+    for (int item = tid; item < NB + NQ; item += NT) {
+      if (item < NB) {
+        const int a = item / H, b = item - (item / H) * H;
+        int i, mi, j, mj;
+        inner_pair<P>(cross, a, ir, i, mi);
+        inner_pair<P>(cross, b, ir, j, mj);
+        float ca, sa, cb, sb;
+        int cla, clb;
+        rot_fast<P>(G, i, mi, tabs, tol2, early2, ca, sa, cla);
+        rot_fast<P>(G, j, mj, tabs, tol2, early2, cb, sb, clb);
+        if (a == b) rot = max(rot, cla);
+        // x_i' = c x_i - s x_mi, x_mi' = s x_i + c x_mi on both sides
+        const float g00 = G[i * P + j], g01 = G[i * P + mj], g10 = G[mi * P + j], g11 = G[mi * P + mj];
+        const float r0j = cb * g00 - sb * g01, r0m = sb * g00 + cb * g01;   // row i after the column rotation
+        const float r1j = cb * g10 - sb * g11, r1m = sb * g10 + cb * g11;   // row mi
+        Gn[i * P + j] = ca * r0j - sa * r1j;
+        Gn[i * P + mj] = ca * r0m - sa * r1m;
+        Gn[mi * P + j] = sa * r0j + ca * r1j;
+        Gn[mi * P + mj] = sa * r0m + ca * r1m;
+      } else {
+        const int e = item - NB;
+        const int r = e / H, b = e - (e / H) * H;
+        int j, mj;
+        inner_pair<P>(cross, b, ir, j, mj);
+        float cb, sb;
+        int clb;
+        rot_fast<P>(G, j, mj, tabs, tol2, early2, cb, sb, clb);
+        const float q0 = Q[r * P + j], q1 = Q[r * P + mj];
+        Q[r * P + j] = cb * q0 - sb * q1;
+        Q[r * P + mj] = sb * q0 + cb * q1;
       }
-      sc[p] = c;
-      so[p] = -s;
-      sc[q] = c;
-      so[q] = s;
     }
-    __syncwarp();
-    for (int idx = lane; idx < H * H; idx += 32) {
-      const int a = idx / H, b = idx - (idx / H) * H;
-      int i, mi, j, mj;
-      inner_pair<P>(cross, a, ir, i, mi);
-      inner_pair<P>(cross, b, ir, j, mj);
-      const float g00 = G[i * P + j], g01 = G[i * P + mj], g10 = G[mi * P + j], g11 = G[mi * P + mj];
-      const float ci = sc[i], si = so[i], cmi = sc[mi], smi = so[mi];
-      const float cj = sc[j], sj = so[j], cmj = sc[mj], smj = so[mj];
-      G[i * P + j] = ci * (cj * g00 + sj * g01) + si * (cj * g10 + sj * g11);
-      G[i * P + mj] = ci * (cmj * g01 + smj * g00) + si * (cmj * g11 + smj * g10);
-      G[mi * P + j] = cmi * (cj * g10 + sj * g11) + smi * (cj * g00 + sj * g01);
-      G[mi * P + mj] = cmi * (cmj * g11 + smj * g10) + smi * (cmj * g01 + smj * g00);
-    }
-    for (int idx = lane; idx < P * H; idx += 32) {
-      const int r = idx / H, b = idx - (idx / H) * H;
-      int j, mj;
-      inner_pair<P>(cross, b, ir, j, mj);
-      const float q0 = Q[r * P + j], q1 = Q[r * P + mj];
-      Q[r * P + j] = sc[j] * q0 + so[j] * q1;
-      Q[r * P + mj] = sc[mj] * q1 + so[mj] * q0;
-    }
-    __syncwarp();
+    __syncthreads();
+    float* t = G;
+    G = Gn;
+    Gn = t;
   }
   rot = __reduce_max_sync(0xffffffffu, rot);
-  if (lane == 0) {
-    *rot_flag = max(*rot_flag, rot);
-    *pair_rot = rot > 0 ? 1 : 0;
+  if ((tid & 31) == 0 && rot > 0) {
+    atomicMax(rot_flag, rot);
+    *pair_rot = 1;
   }
+}
+
+// One Newton-Schulz step on the accumulated rotation Q of a block pair
+// (P x P, row-major, shared memory), by the whole CTA: W = Q^T Q, then
+// Qo = Q (3 I - W) / 2.  Q is a product of FP32 rotations whose c^2 + s^2
+// misses 1 by about an ulp, with a fixed sign for the small angles of the
+// late sweeps (c rounds to 1), so without this step every round would scale
+// the columns of K and V by that much and a column that takes part in
+// thousands of rounds would drift by thousands of ulps; after it Q is
+// orthonormal to rounding, whose error has no preferred sign.  Returns Qo.
+template <int P, int NT>
+__device__ __forceinline__ float* ns_orthonormalize(const float* Q, float* W, float* Qo, int tid) {
+  for (int e = tid; e < P * P; e += NT) {
+    const int i = e / P, j = e % P;
+    float acc = 0.f;
+#pragma unroll 4
+    for (int r = 0; r < P; ++r) acc = fmaf(Q[r * P + i], Q[r * P + j], acc);
+    W[e] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < P * P; e += NT) {
+    const int r = e / P, j = e % P;
+    float acc = 0.f;
+#pragma unroll 4
+    for (int c = 0; c < P; ++c) acc = fmaf(Q[r * P + c], W[c * P + j], acc);
+    Qo[e] = fmaf(-0.5f, acc, 1.5f * Q[e]);
+  }
+  __syncthreads();
+  return Qo;
 }
 
 // Host side, shared by the two core kernels (defined in jacobi_block.cu):

@@ -2,10 +2,11 @@
 // picks on the GPU and the library reads.
 //
 // A plain-text file, one entry per line ('#' starts a comment):
-//   core  <n_max> <panel> <parts> <resident> <warp>
+//   core  <n_max> <panel> <parts> <resident> <fast>
 //         FP32 core SVD of an n x n core, n <= n_max (first matching line):
 //         panel 16 | 32, parts 0..8 CTAs per cluster, resident 0 | 1,
-//         warp 0 | 1 (the Gram sweep by one warp)
+//         fast 0 | 1 (the Gram sweep with one barrier per inner round and
+//         fast rotations)
 //   chunk <prec> <phase> <k_max> <c>
 //         border rows (phase 0, Eq. 2) / columns (phase 1, Eq. 3) appended per
 //         incremental step when the caller passes 0, for a phase whose target
@@ -35,7 +36,7 @@ namespace fastpi {
 namespace {
 
 struct CoreRow {
-  int n_max, panel, parts, resident, warp;
+  int n_max, panel, parts, resident, fast;
 };
 struct ChunkRow {
   int prec, phase;
@@ -89,7 +90,7 @@ bool parse(const std::string& path, Table& t, std::string* why) {
     bool ok = false;
     if (kind == "core") {
       CoreRow r;
-      ok = bool(ss >> r.n_max >> r.panel >> r.parts >> r.resident >> r.warp) && (r.panel == 16 || r.panel == 32) &&
+      ok = bool(ss >> r.n_max >> r.panel >> r.parts >> r.resident >> r.fast) && (r.panel == 16 || r.panel == 32) &&
            r.parts >= 0 && r.parts <= 8 && r.n_max >= 2;
       if (ok) out.core.push_back(r);
     } else if (kind == "chunk") {
@@ -135,7 +136,7 @@ bool tuned_core_tiling(int n, CoreTiling* out) {
       out->panel = r.panel;
       out->parts = r.parts;
       out->resident = r.resident != 0;
-      out->warp_solve = r.warp != 0;
+      out->fast_solve = r.fast != 0;
       return true;
     }
   return false;

@@ -147,7 +147,7 @@ def gemm_f32(A: torch.Tensor, B: torch.Tensor, ta: bool = False, tb: bool = Fals
     return Cout
 
 
-def core_svd_f32(K: torch.Tensor, panel: int = 16, parts: int = 0, resident: bool = False, warp: bool = True,
+def core_svd_f32(K: torch.Tensor, panel: int = 16, parts: int = 0, resident: bool = False, fast: bool = True,
                  single_cta: bool = False):
     """SVD of a square FP32 matrix by the library's core-SVD kernel (block
     one-sided Jacobi) with the given tiling.  K: n x n CUDA tensor (any float
@@ -161,7 +161,7 @@ def core_svd_f32(K: torch.Tensor, panel: int = 16, parts: int = 0, resident: boo
     V = torch.empty((n, n), dtype=torch.float32, device=K.device)
     S = np.empty(n, dtype=np.float64)
     sw, ms = C.c_int(), C.c_float()
-    flags = (1 if resident else 0) | (0 if warp else 2) | (4 if single_cta else 0)
+    flags = (1 if resident else 0) | (0 if fast else 2) | (4 if single_cta else 0)
     st = torch.cuda.current_stream(K.device).cuda_stream
     with torch.cuda.device(K.device):
         _check(lib().fastpi_core_svd_f32(n, _ptr(Kc), _ptr(U), S.ctypes.data, _ptr(V), int(panel), int(parts), flags,
