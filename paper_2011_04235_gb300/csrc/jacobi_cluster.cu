@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(CT) k_jacobi_cluster(ClArgs a) {
       // one barrier per inner round and fast rotations, or the IEEE form with
       // two barriers per inner round
       float* Qf = Q;
-      if (FAST) {
+      if constexpr (FAST) {
         inner_solve_fast<P, CT>(G, Gn, Q, tid, tabs, tol2, early2, rr != 0, &s_rot, &s_pair_rot);
         __syncthreads();
       } else {
