@@ -522,9 +522,10 @@ __global__ void k_gather_lp(const double* Lo, const int32_t* piv, const int32_t*
 }
 
 // One CTA.
-__global__ void k_scatter_inv(const double* X, const int32_t* piv, const int32_t* rank_p, int c, double* Lio) {
+template <typename E>
+__global__ void k_scatter_inv(const E* X, const int32_t* piv, const int32_t* rank_p, int c, E* Lio) {
   const int rank = *rank_p;
-  for (int64_t e = threadIdx.x; e < int64_t(c) * c; e += blockDim.x) Lio[e] = 0.0;
+  for (int64_t e = threadIdx.x; e < int64_t(c) * c; e += blockDim.x) Lio[e] = E(0);
   __syncthreads();
   for (int64_t e = threadIdx.x; e < int64_t(rank) * rank; e += blockDim.x) {
     const int a = int(e / rank), b = int(e % rank);
@@ -558,9 +559,9 @@ __global__ void k_trinv_cols(const T* __restrict__ L, int c, const int32_t* __re
 
 // K ((k + c) x (k + c), COLUMN-major) = [[diag(sig), P], [0, R_R]] with
 // P = Pt^T (Pt: c x k, ld ldp) and R_R = M^T (M: c x c row-major, FP64).
-template <typename T>
+template <typename T, typename TM>
 __global__ void k_build_core(int64_t k, int64_t c, const double* __restrict__ sig, const T* __restrict__ Pt,
-                             int64_t ldp, const double* __restrict__ M, T* __restrict__ K) {
+                             int64_t ldp, const TM* __restrict__ M, T* __restrict__ K) {
   const int64_t n = k + c;
   int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= n * n) return;
@@ -761,10 +762,22 @@ struct Phase {
                                                piv.get(), rk.get());
       CK_LAUNCH();
     }
-    trinv(Lp.get(), kept.get(), X.get());
-    k_scatter_inv<<<1, 1024, 0, st>>>(X.get(), piv.get(), rk.get(), int(c), Linv.get());
-    CK_LAUNCH();
-    to_T(Linv.get(), LinvT.get());
+    if constexpr (sizeof(T) == 8) {
+      trinv(Lp.get(), kept.get(), X.get());
+      k_scatter_inv<double><<<1, 1024, 0, st>>>(X.get(), piv.get(), rk.get(), int(c), Linv.get());
+      CK_LAUNCH();
+      to_T(Linv.get(), LinvT.get());
+    } else {
+      // mixed: the inverse of the kept triangle in FP32 -- its error, like that
+      // of the FP32 product below, only perturbs the orthogonality of Q1, which
+      // the second pass restores
+      DArr<float> Lp32(c * c, st), X32(c * c, st);
+      k_convert<float, double><<<g1(c * c), 256, 0, st>>>(c * c, Lp.get(), Lp32.get());
+      CK_LAUNCH();
+      trinv(Lp32.get(), kept.get(), X32.get());
+      k_scatter_inv<float><<<1, 1024, 0, st>>>(X32.get(), piv.get(), rk.get(), int(c), LinvT.get());
+      CK_LAUNCH();
+    }
     gemm_t<T>(st, false, true, p, c, c, T(1), D.get(), c, LinvT.get(), c, T(0), Q1.get(), c);
     // second pass: Q1 is orthonormal up to rounding, its Gram ~ I is well
     // conditioned, so this Cholesky runs in the storage precision
@@ -781,18 +794,23 @@ struct Phase {
     }
     trinv(GT.get(), kept2.get(), LinvT.get());
     gemm_t<T>(st, false, true, p, c, c, T(1), Q1.get(), c, LinvT.get(), c, T(0), Q.get(), c);
-    if (sizeof(T) == 8) {
+    // R_R = (Lo L2)^T : M = Lo * L2 (FP64 in the FP64 form; in the mixed form
+    // in FP32 on the tensor cores, the precision of the core it feeds)
+    DArr<T> K(n * n, st), J(n * n, st);
+    if constexpr (sizeof(T) == 8) {
       CK(cudaMemcpyAsync(G2.get(), GT.get(), size_t(c * c) * 8, cudaMemcpyDeviceToDevice, st));
+      gemm<double>(st, false, false, c, c, c, 1.0, Lo.get(), c, G2.get(), c, 0.0, M.get(), c);
+      k_build_core<T, double><<<g1(n * n), 256, 0, st>>>(k, c, S(), Pt.get(), ldp, M.get(), K.get());
+      CK_LAUNCH();
     } else {
-      k_convert<double, T><<<g1(c * c), 256, 0, st>>>(c * c, GT.get(), G2.get());
+      DArr<float> Lo32(c * c, st), M32(c * c, st);
+      k_convert<float, double><<<g1(c * c), 256, 0, st>>>(c * c, Lo.get(), Lo32.get());
+      CK_LAUNCH();
+      gemm_f32(st, false, false, c, c, c, 1.f, Lo32.get(), c, GT.get(), c, 0.f, M32.get(), c);
+      k_build_core<T, float><<<g1(n * n), 256, 0, st>>>(k, c, S(), Pt.get(), ldp, M32.get(), K.get());
       CK_LAUNCH();
     }
-    // R_R = (Lo L2)^T : M = Lo * L2
-    gemm<double>(st, false, false, c, c, c, 1.0, Lo.get(), c, G2.get(), c, 0.0, M.get(), c);
     // core SVD
-    DArr<T> K(n * n, st), J(n * n, st);
-    k_build_core<T><<<g1(n * n), 256, 0, st>>>(k, c, S(), Pt.get(), ldp, M.get(), K.get());
-    CK_LAUNCH();
     DArr<double> jsig(n, st);
     DArr<int32_t> jperm(n, st);
     JacobiStats js;

@@ -315,7 +315,8 @@ __global__ void __launch_bounds__(256) k_jacobi(const DevProb<T>* __restrict__ p
 
 // Per problem: sigma_j = |b_j| and a descending sort (ties: lower index first).
 template <typename T>
-__global__ void k_finish(const DevProb<T>* probs, const int64_t* sig_off, double* sig, int32_t* perm, int nq_max) {
+__global__ void k_finish(const DevProb<T>* probs, const int64_t* sig_off, double* sig, int32_t* perm, int nq_max,
+                         const double* norms) {
   extern __shared__ unsigned char smem_raw[];
   const DevProb<T> pr = probs[blockIdx.x];
   int nq = 1;
@@ -323,19 +324,27 @@ __global__ void k_finish(const DevProb<T>* probs, const int64_t* sig_off, double
   double* key = reinterpret_cast<double*>(smem_raw);
   int* idx = reinterpret_cast<int*>(key + nq_max);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int j = w; j < nq; j += nwarp) {
-    double s = 0;
-    if (j < pr.q) {
-      const T* col = pr.A + int64_t(j) * pr.lda;
-      for (int r = lane; r < pr.p; r += 32) {
-        double x = double(__ldcg(col + r));
-        s += x * x;
-      }
-      s = warp_sum(s);
-    }
-    if (lane == 0) {
-      key[j] = j < pr.q ? sqrt(s) : -1.0;
+  if (norms) {
+    // column norms computed beforehand (a single large problem: k_colnorms)
+    for (int j = threadIdx.x; j < nq; j += blockDim.x) {
+      key[j] = j < pr.q ? norms[j] : -1.0;
       idx[j] = j;
+    }
+  } else {
+    for (int j = w; j < nq; j += nwarp) {
+      double s = 0;
+      if (j < pr.q) {
+        const T* col = pr.A + int64_t(j) * pr.lda;
+        for (int r = lane; r < pr.p; r += 32) {
+          double x = double(__ldcg(col + r));
+          s += x * x;
+        }
+        s = warp_sum(s);
+      }
+      if (lane == 0) {
+        key[j] = j < pr.q ? sqrt(s) : -1.0;
+        idx[j] = j;
+      }
     }
   }
   __syncthreads();
@@ -365,6 +374,23 @@ __global__ void k_finish(const DevProb<T>* probs, const int64_t* sig_off, double
     sig[o + t] = key[t];
     perm[o + t] = idx[t];
   }
+}
+
+// |A[:, j]| for the q columns of one p x q problem, one warp per column (many
+// CTAs: the norms of a single large problem off the sort's critical path).
+template <typename T>
+__global__ void k_colnorms(const T* __restrict__ A, int64_t lda, int p, int q, double* __restrict__ out) {
+  const int j = int(blockIdx.x) * int(blockDim.x >> 5) + int(threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (j >= q) return;
+  const T* col = A + int64_t(j) * lda;
+  double s = 0;
+  for (int r = lane; r < p; r += 32) {
+    const double x = double(__ldcg(col + r));
+    s += x * x;
+  }
+  s = warp_sum(s);
+  if (lane == 0) out[j] = sqrt(s);
 }
 
 template <typename T> struct Eps;
@@ -492,7 +518,14 @@ JacobiStats run_bucket(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& probs
   while (nq_max < maxq) nq_max <<= 1;
   size_t smem = size_t(nq_max) * (sizeof(double) + sizeof(int));
   if (smem > 48 * 1024) allow_max_dynamic_smem((const void*)k_finish<T>);
-  k_finish<T><<<nprob, 512, smem, st>>>(d_probs, d_sig_off, sig, perm, nq_max);
+  DArr<double> norms;
+  if (nprob == 1) {
+    norms = DArr<double>(probs[0].q, st);
+    k_colnorms<T><<<unsigned((probs[0].q + 7) / 8), 256, 0, st>>>(probs[0].A, probs[0].lda, probs[0].p, probs[0].q,
+                                                                    norms.get());
+    CK_LAUNCH();
+  }
+  k_finish<T><<<nprob, 512, smem, st>>>(d_probs, d_sig_off, sig, perm, nq_max, nprob == 1 ? norms.get() : nullptr);
   CK_LAUNCH();
 
   unsigned stat = 0;
@@ -589,7 +622,14 @@ void jacobi_sort_columns(fastpi_ctx* h, const std::vector<JacobiProblem<T>>& pro
   while (nq_max < maxq) nq_max <<= 1;
   size_t smem = size_t(nq_max) * (sizeof(double) + sizeof(int));
   if (smem > 48 * 1024) allow_max_dynamic_smem((const void*)k_finish<T>);
-  k_finish<T><<<nprob, 512, smem, st>>>(d_probs, d_sig_off, sig, perm, nq_max);
+  DArr<double> norms;
+  if (nprob == 1) {
+    norms = DArr<double>(probs[0].q, st);
+    k_colnorms<T><<<unsigned((probs[0].q + 7) / 8), 256, 0, st>>>(probs[0].A, probs[0].lda, probs[0].p, probs[0].q,
+                                                                    norms.get());
+    CK_LAUNCH();
+  }
+  k_finish<T><<<nprob, 512, smem, st>>>(d_probs, d_sig_off, sig, perm, nq_max, nprob == 1 ? norms.get() : nullptr);
   CK_LAUNCH();
 }
 
