@@ -54,7 +54,14 @@ def _errors(K64, **tiling):
     Kf = K64.astype(np.float32)
     n = Kf.shape[0]
     ref = np.linalg.svd(Kf.astype(np.float64), compute_uv=False)
-    S, U, V, sweeps, ms = fp.core_svd_f32(torch.from_numpy(Kf).cuda(), **tiling)
+    try:
+        S, U, V, sweeps, ms = fp.core_svd_f32(torch.from_numpy(Kf).cuda(), **tiling)
+    except fp.FastPIError as e:
+        # a tiling whose clusters cannot all be resident at once (or whose
+        # panels do not fit) is refused, not run: nothing to check
+        if e.status == 1 and "does not fit" in str(e):
+            pytest.skip(f"tiling does not fit this core: {tiling}")
+        raise
     U = U.double().cpu().numpy()
     V = V.double().cpu().numpy()
     s1 = ref[0]
