@@ -458,7 +458,13 @@ bool launch_cluster(fastpi_ctx* hc, float* K, float* V, int n, int parts, Jacobi
     return false;
   }
   if (ncl < slots) return false;
-  cfg.numAttrs = 2;
+  // the CTAs wait on one another, so the launch is cooperative (all clusters
+  // resident at once, also beside other instances' kernels on other streams);
+  // FASTPI_CORE_NOCOOP=1 drops that attribute for profilers that do not pass
+  // a cooperative cluster launch through (a single instance alone on the GPU
+  // still finds every cluster resident: checked above)
+  const char* nc = std::getenv("FASTPI_CORE_NOCOOP");
+  cfg.numAttrs = (nc && nc[0] == '1' && nc[1] == 0) ? 1 : 2;
 
   DArr<BBar> gb(1, st);
   constexpr int NPART = 128;
@@ -509,7 +515,12 @@ bool launch_cluster(fastpi_ctx* hc, float* K, float* V, int n, int parts, Jacobi
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
   if (stat & ST_BARRIER_TIMEOUT) fail(FASTPI_ERR_NO_CONVERGENCE, "cluster Jacobi SVD: a bounded wait timed out");
-  if (stat & ST_BAD_INDEX) fail(FASTPI_ERR_CUDA, "cluster Jacobi SVD: launched with clusters of the wrong size");
+  if (stat & ST_BAD_INDEX) {
+    // the launch did not get its clusters (the kernel left at once, before
+    // touching K or V): the caller takes the single-CTA kernel
+    CK(cudaMemsetAsync(hc->dstatus.get(), 0, 4, st));
+    return false;
+  }
 #ifdef FASTPI_PHASE_CLOCKS
   {
     long long clk[8] = {0};
