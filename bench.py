@@ -219,8 +219,9 @@ def oracle_sample(w, chunks, budget_s: float = 60.0):
 # DRAM bytes (read + write) per launch of the dominant kernel, from an ncu
 # capture of the current kernel on this workload; None whenever the kernel's
 # source changed after the capture, until it is captured again.
-JACOBI_TRAFFIC_BYTES = None
-JACOBI_TRAFFIC_SOURCE = "null: the kernel changed after the last ncu capture"
+JACOBI_TRAFFIC_BYTES = 924.038052e6 * 3.155264e-3
+JACOBI_TRAFFIC_SOURCE = ("ncu dram__bytes.sum.per_second x gpu__time_duration.sum of one k_jacobi_cluster<16, 0, 1> "
+                         "launch (the first row-phase core, n = 531) of this workload")
 
 
 def pinv_threshold_report(S, m, n):
@@ -440,7 +441,8 @@ def main():
     achieved = core["flops"] / (core["ms"] / 1000.0) / 1e12 if core["ms"] > 0 else 0.0
     achieved_rot = core["flops_rot"] / (core["ms"] / 1000.0) / 1e12 if core["ms"] > 0 else 0.0
     step_s = max(sum(t_mixed), 1e-9)
-    roofline = {"kernel": "k_jacobi_block (block one-sided Jacobi SVD of the update cores, FP32)", "bound": "alu",
+    roofline = {"kernel": "k_jacobi_cluster (block one-sided Jacobi SVD of the update cores, a block pair's rows "
+                          "split over a thread-block cluster, FP32)", "bound": "alu",
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                 "traffic": JACOBI_TRAFFIC_BYTES, "traffic_source": JACOBI_TRAFFIC_SOURCE,
                 "work_per_launch": "12 n^3 flops for an n x n core (n = k + c)",
@@ -474,7 +476,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": bench_config(w, chunks),
             "precision": "mixed: FP32 storage, TF32 tensor-core products (split hi/lo, 3 passes) with FP32 "
-                         "accumulation, FP64-accumulated Gram and FP64 Cholesky, FP32 block-Jacobi core SVD",
+                         "accumulation, float-float residual Gram and FP64 pivoted Cholesky, FP32 block-Jacobi "
+                         "core SVD (cluster form, Newton-Schulz re-orthonormalised rotations)",
             "mixed": {"seconds": sec_mixed, "gflops": F / sec_mixed / 1e9, "residual": res_mixed,
                       "stage_ms": {k: info[k] for k in info if k.startswith("ms_")}},
             "fp64": {"seconds": statistics.mean(t64), "gflops": F / statistics.mean(t64) / 1e9,
