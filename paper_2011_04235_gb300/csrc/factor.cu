@@ -27,6 +27,7 @@
 #include <condition_variable>
 #include <type_traits>
 
+#include "cholqr.cuh"
 #include "dense.cuh"
 #include "factor.cuh"
 #include "jacobi.cuh"
@@ -724,11 +725,17 @@ struct Phase {
     };
     auto trinv = [&](auto* L, const int32_t* kp, auto* Xo) {
       using E = std::remove_pointer_t<decltype(L)>;
-      const size_t sm = size_t(c) * sizeof(E);
-      if (sm > 48 * 1024)
-        allow_max_dynamic_smem((const void*)k_trinv_cols<E>);
-      k_trinv_cols<E><<<unsigned(c), 32, sm, st>>>(L, int(c), kp, Xo);
-      CK_LAUNCH();
+      int max_smem = 0;
+      CK(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+      if (trinv_blocked_smem(int(c), sizeof(E)) + 1024 <= size_t(max_smem)) {
+        trinv_blocked<E>(st, L, int(c), kp, Xo);   // 32-column blocks
+      } else {
+        const size_t sm = size_t(c) * sizeof(E);
+        if (sm > 48 * 1024)
+          allow_max_dynamic_smem((const void*)k_trinv_cols<E>);
+        k_trinv_cols<E><<<unsigned(c), 32, sm, st>>>(L, int(c), kp, Xo);
+        CK_LAUNCH();
+      }
     };
     auto to_T = [&](const double* src, T* dst) {
       if (sizeof(T) == 8) {
@@ -783,7 +790,13 @@ struct Phase {
     // conditioned, so this Cholesky runs in the storage precision
     gemm_t<T>(st, true, false, c, c, p, T(1), Q1.get(), c, Q1.get(), c, T(0), GT.get(), c);
     const size_t packed = (size_t(c) * (c + 1) / 2 + size_t(c)) * sizeof(T);
-    if (packed <= 200 * 1024) {
+    int max_smem_b = 0;
+    CK(cudaDeviceGetAttribute(&max_smem_b, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if (sizeof(T) == 4 && chol_drop_blocked_smem(int(c)) + 16 * 1024 <= size_t(max_smem_b)) {
+      // blocked by 32 columns, the packed triangle in shared memory
+      chol_drop_blocked(st, reinterpret_cast<float*>(GT.get()), int(c), float(DROP_ABS_PASS2), kept2.get(),
+                        rk.get() + 1);
+    } else if (packed <= 200 * 1024) {
       if (packed > 48 * 1024)
         allow_max_dynamic_smem((const void*)k_chol_drop_smem<T>);
       k_chol_drop_smem<T><<<1, 1024, packed, st>>>(GT.get(), int(c), DROP_ABS_PASS2, kept2.get(), rk.get() + 1);
