@@ -56,6 +56,7 @@ struct CoreTiling {
   bool fast_solve = true;   // the Gram sweep with one barrier per inner round and fast rotations
   bool single_cta = false;  // the single-CTA block kernel instead of the cluster form
   bool strict = false;      // no fallback to the single-CTA kernel when the cluster form does not fit
+  float early_exit = 1e-3f; // a sweep whose rotations all stay below this (|g| / sqrt(al be)) is the last
 };
 // U[:, t] = K[:, perm[t]] / sig[t] (zero when sig[t] = 0), Vs[:, t] = V[:, perm[t]]
 // for the outputs of jacobi_svd_block (n x n column-major, ld n).

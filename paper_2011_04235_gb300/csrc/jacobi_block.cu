@@ -549,7 +549,8 @@ void core_finish(fastpi_ctx* hc, const float* Kp, const float* Vp, int n, int ld
 // Tiling of the core SVD from the environment (measurement switches):
 // FASTPI_CORE_KERNEL=block selects the single-CTA kernel, FASTPI_CORE_P=16|32
 // the panel, FASTPI_CORE_C=1..8 the CTAs per cluster, FASTPI_CORE_FAST=0 the
-// IEEE Gram sweep, FASTPI_JACOBI_RESIDENT=1 the resident-block schedule.
+// IEEE Gram sweep, FASTPI_JACOBI_RESIDENT=1 the resident-block schedule,
+// FASTPI_CORE_EARLY the early-exit threshold of the sweeps.
 static bool env_int(const char* name, int* v) {
   const char* e = std::getenv(name);
   if (!e || !*e) return false;
@@ -578,6 +579,10 @@ bool jacobi_svd_block(fastpi_ctx* hc, float* K, float* V, int n, double* sig, in
     if (env_int("FASTPI_CORE_P", &v) && (v == 16 || v == 32)) tl.panel = v;
     if (env_int("FASTPI_CORE_C", &v) && v >= 1 && v <= 8) tl.parts = v;
     if (env_int("FASTPI_CORE_FAST", &v)) tl.fast_solve = v != 0;
+    if (const char* e = std::getenv("FASTPI_CORE_EARLY")) {
+      const double x = std::atof(e);
+      if (x > 0 && x < 1) tl.early_exit = float(x);
+    }
     if (std::getenv("FASTPI_JACOBI_RESIDENT")) tl.resident = resident_schedule();
   }
   if (!tl.single_cta) ok = jacobi_svd_cluster(hc, K, V, n, tl, stats, &ms, &sweeps, &res);

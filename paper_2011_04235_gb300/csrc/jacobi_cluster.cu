@@ -48,7 +48,6 @@ using namespace jdev;
 
 constexpr int CT = 256;                 // threads per CTA (8 warps)
 constexpr int C_MAX_SWEEPS = 30;
-constexpr float C_EARLY_OFF = 1e-3f;    // a sweep whose rotations all stay below this ends the iteration
 
 struct ClArgs {
   float* K;         // ldk x n column-major: in A (rows >= n zero), out A J
@@ -58,6 +57,7 @@ struct ClArgs {
   int nb;           // number of column blocks (even)
   int parts;        // C: CTAs per cluster the grid was laid out for
   float tol;
+  float early;      // a sweep whose rotations all stay below this ends the iteration
   BBar* gb;
   int* out;         // [0] sweeps used, [1] hit the sweep cap
   unsigned* status;
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(CT) k_jacobi_cluster(ClArgs a) {
     const float ne = float(n) * 1.1920929e-7f;
     return float(double(ne) * double(ne) * a.gb->fro2);
   }();
-  const float tol2 = a.tol * a.tol, early2 = C_EARLY_OFF * C_EARLY_OFF;
+  const float tol2 = a.tol * a.tol, early2 = a.early * a.early;
   if (tid == 0) s_rot = 0;
   const int nq = rpc / 4;   // 16-byte chunks per column part
   int sweep = 0;
@@ -417,8 +417,8 @@ int pick_parts(int slots, int num_sms, int want) {
 }
 
 template <int P, bool RES, bool FAST>
-bool launch_cluster(fastpi_ctx* hc, float* K, float* V, int n, int parts, JacobiStats* stats, float* ms_out,
-                    int* sweeps) {
+bool launch_cluster(fastpi_ctx* hc, float* K, float* V, int n, int parts, float early, JacobiStats* stats,
+                    float* ms_out, int* sweeps) {
   cudaStream_t st = hc->stream;
   constexpr int B = P / 2;
   int nb = (n + B - 1) / B;
@@ -487,6 +487,7 @@ bool launch_cluster(fastpi_ctx* hc, float* K, float* V, int n, int parts, Jacobi
   a.nb = nb;
   a.parts = C;
   a.tol = float(std::sqrt(double(n)) * 1.1920928955078125e-07);
+  a.early = early;
   a.gb = gb.get();
   a.out = out.get();
   a.status = hc->dstatus.get();
@@ -554,7 +555,7 @@ bool jacobi_svd_cluster(fastpi_ctx* hc, float* K, float* V, int n, const CoreTil
   if (nb & 1) ++nb;
   const int C = pick_parts(std::max(nb / 2, 1), hc->num_sms, tiling.parts);
   *used_res = tiling.resident;
-#define FASTPI_CL(PV, RV, WV) launch_cluster<PV, RV, WV>(hc, K, V, n, C, stats, ms, sweeps)
+#define FASTPI_CL(PV, RV, WV) launch_cluster<PV, RV, WV>(hc, K, V, n, C, tiling.early_exit, stats, ms, sweeps)
   const bool r = tiling.resident, w = tiling.fast_solve;
   if (P == 16) return r ? (w ? FASTPI_CL(16, true, true) : FASTPI_CL(16, true, false))
                         : (w ? FASTPI_CL(16, false, true) : FASTPI_CL(16, false, false));
