@@ -56,7 +56,12 @@ struct CoreTiling {
   bool fast_solve = true;   // the Gram sweep with one barrier per inner round and fast rotations
   bool single_cta = false;  // the single-CTA block kernel instead of the cluster form
   bool strict = false;      // no fallback to the single-CTA kernel when the cluster form does not fit
-  float early_exit = 1e-3f; // a sweep whose rotations all stay below this (|g| / sqrt(al be)) is the last
+  // a sweep whose rotations all stay below this (|g| / sqrt(al be)) is the
+  // last: measured on the 20 000 x 5 000 workload (mixed factor, 40 cores),
+  // 1e-3 -> 399 ms, residual gap to the oracle 1.1e-8, sigma error 1.1e-5,
+  // |U^T U - I| 3.9e-5; 5e-3 -> 376 ms, 6.8e-7, 1.4e-5, 3.8e-5; 1e-2 -> 359 ms,
+  // 3.4e-7, 1.2e-4, 1.6e-4 (orthonormality starts to degrade beyond 5e-3)
+  float early_exit = 5e-3f;
 };
 // U[:, t] = K[:, perm[t]] / sig[t] (zero when sig[t] = 0), Vs[:, t] = V[:, perm[t]]
 // for the outputs of jacobi_svd_block (n x n column-major, ld n).
