@@ -74,7 +74,7 @@ def run_many(count: int, prec: str, concurrency: list):
         res[f"max_rel_residual_diff_concurrency_{conc}"] = gap
     ck.__exit__(None, None, None)
     res["clocks"] = ck.summary()
-    res["residual_sum_sequential"] = float(sum(seq_res))
+    res["residuals_sequential"] = [float(x) for x in seq_res]
     print(json.dumps(res))
 
 
