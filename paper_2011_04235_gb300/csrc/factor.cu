@@ -477,6 +477,9 @@ __global__ void __launch_bounds__(PCHOL_THREADS) k_pchol_panel(const double* __r
       break;
     }
     const double ljj = sqrt(best);
+    // one reciprocal instead of a division per row (GB300's FP64 pipe runs at
+    // 1/64 of its FP32 rate, and an FP64 division is a sequence of FMAs)
+    const double rljj = 1.0 / ljj;
     // column t for every unused row other than the pivot: the Schur complement
     // column of pivot j (row j of G, by symmetry) minus this panel's earlier columns
     for (int i = tid; i < c; i += PCHOL_THREADS) {
@@ -488,7 +491,7 @@ __global__ void __launch_bounds__(PCHOL_THREADS) k_pchol_panel(const double* __r
       if (used_s[i]) continue;
       double sacc = G[int64_t(j) * c + i];
       for (int q = 0; q < k; ++q) sacc -= pan[i * PCHOL_PS + q] * pan[j * PCHOL_PS + q];
-      const double lit = sacc / ljj;
+      const double lit = sacc * rljj;
       pan[i * PCHOL_PS + k] = lit;
       d_s[i] -= lit * lit;
     }
@@ -508,6 +511,23 @@ __global__ void __launch_bounds__(PCHOL_THREADS) k_pchol_panel(const double* __r
     used[i] = used_s[i];
   }
   if (tid == 0 && stop) state[0] = 1;
+}
+
+// G[i, l] -= sum_{q in [t0, t0 + nb)} Lo[i, q] Lo[l, q] for all i, l < c: the
+// Schur-complement update after a panel of k_pchol_panel, one thread per entry
+// so that the FP64 work spreads over every SM (a tiled GEMM of this c x c x 32
+// shape has too few tiles to do so).  Skipped once the factorization stopped.
+__global__ void k_pchol_trailing(double* __restrict__ G, int c, int t0, int nb, const double* __restrict__ Lo,
+                                 const int32_t* __restrict__ state) {
+  if (state[0]) return;
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= int64_t(c) * c) return;
+  const int i = int(e / c), l = int(e % c);
+  const double* Li = Lo + int64_t(i) * c + t0;
+  const double* Ll = Lo + int64_t(l) * c + t0;
+  double s = 0.0;
+  for (int q = 0; q < nb; ++q) s = fma(Li[q], Ll[q], s);
+  G[e] -= s;
 }
 
 // Lp[a, b] = Lo[piv[a], b] for b <= a < rank (zero elsewhere); rank = state[1].
@@ -759,8 +779,10 @@ struct Phase {
                                                   used.get(), Lo.get(), piv.get(), kept.get(), pstate.get());
         CK_LAUNCH();
         const int64_t nbp = std::min<int64_t>(PCHOL_NB, c - t0);
-        if (t0 + nbp < c)
-          gemm<double>(st, false, true, c, c, nbp, -1.0, Lo.get() + t0, c, Lo.get() + t0, c, 1.0, G.get(), c);
+        if (t0 + nbp < c) {
+          k_pchol_trailing<<<g1(c * c), 256, 0, st>>>(G.get(), int(c), int(t0), int(nbp), Lo.get(), pstate.get());
+          CK_LAUNCH();
+        }
       }
       k_gather_lp<<<g1(c * c), 256, 0, st>>>(Lo.get(), piv.get(), pstate.get(), int(c), Lp.get(), rk.get());
       CK_LAUNCH();
