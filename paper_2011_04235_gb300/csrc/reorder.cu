@@ -216,13 +216,14 @@ __global__ void k_cc_label(const uint8_t* act, int64_t N, int32_t* parent, int32
 }
 
 __global__ void k_gcc(const uint8_t* act, const int32_t* label, const int32_t* cntT, const int32_t* cntF,
-                      int64_t N, unsigned long long* best) {
+                      int64_t N, unsigned long long* best, int32_t* nroots) {
   int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (v >= N) return;
   if (act[v] && label[v] == int32_t(v)) {
     unsigned long long size = unsigned(cntT[v] + cntF[v]);
     unsigned long long key = (size << 32) | (0xFFFFFFFFull - unsigned(v));
     atomicMax(best, key);
+    atomicAdd(nroots, 1);
   }
 }
 
@@ -252,12 +253,16 @@ __global__ void k_keep_gcc(uint8_t* act, const int32_t* label, int32_t gcc, int6
   if (v < N && act[v]) act[v] = (label[v] == gcc) ? 1 : 0;
 }
 
-__global__ void k_summary(const unsigned long long* best, const int32_t* cntT, const int32_t* cntF, int64_t* out) {
+// out = {GCC label (-1: G' empty), its instances, its features, the number of
+// the other (non-giant) components}
+__global__ void k_summary(const unsigned long long* best, const int32_t* cntT, const int32_t* cntF,
+                          const int32_t* nroots, int64_t* out) {
   unsigned long long b = *best;
   int32_t gcc = b ? int32_t(0xFFFFFFFFull - (b & 0xFFFFFFFFull)) : -1;
   out[0] = gcc;
   out[1] = gcc >= 0 ? cntT[gcc] : 0;
   out[2] = gcc >= 0 ? cntF[gcc] : 0;
+  out[3] = *nroots - (gcc >= 0 ? 1 : 0);
 }
 
 __global__ void k_inverse_perm(const int32_t* order, int64_t n, int32_t* pos) {
@@ -340,22 +345,23 @@ void run_reorder(fastpi_ctx* h, double k, Reordering& R) {
   DArr<uint32_t> ids(cap, st), keys(cap, st);
   DArr<int64_t> bT(cap, st), bF(cap, st), d_row_off(cap + 1, st), d_col_off(cap + 1, st), summ(4, st);
   DArr<unsigned long long> best(1, st);
+  DArr<int32_t> dnroots(1, st);
   CK(cudaMemsetAsync(d_row_off.get(), 0, 8, st));
   CK(cudaMemsetAsync(d_col_off.get(), 0, 8, st));
 
-  // compact the active nodes of one side (plus keys), sort, return count
+  // compact the active nodes of one side (plus keys); `known` is the number
+  // of nodes that pass, which the host always knows from the counts of the
+  // iteration (active instances / features, the GCC's size), so no read-back
   auto compact = [&](int64_t base, int64_t cnt, const int32_t* lab, int32_t gcc, const int32_t* keysrc,
-                     int32_t key_bias, int key_neg) -> int64_t {
-    if (cnt == 0) return 0;
+                     int32_t key_bias, int key_neg, int64_t known) -> int64_t {
+    if (cnt == 0 || known == 0) return 0;
     k_flags_active<<<nblk(cnt), BS, 0, st>>>(act, lab, gcc, base, cnt, flags);
     CK_LAUNCH();
     exclusive_scan_i32(flags, pos, cnt, st);
     k_compact<<<nblk(cnt), BS, 0, st>>>(flags, pos, cnt, keysrc, base, key_bias, key_neg, ids,
                                         keysrc ? keys.get() : nullptr, dcount);
     CK_LAUNCH();
-    int32_t c = 0;
-    d2h_sync(&c, dcount, 4, st);
-    return c;
+    return known;
   };
 
   int64_t fT = 0, fF = 0, bTc = m, bFc = n, nb = 0, nI = m, nF = n, it = 0;
@@ -371,14 +377,14 @@ void run_reorder(fastpi_ctx* h, double k, Reordering& R) {
     CK_LAUNCH();
     // hubs: instances (key = n - deg so that ascending key = degree descending)
     if (m_hub > 0) {
-      int64_t c = compact(0, m, nullptr, 0, deg, int32_t(n), 1);
+      int64_t c = compact(0, m, nullptr, 0, deg, int32_t(n), 1, nI);
       radix_sort_pairs(keys, ids, c, bits_for(uint64_t(n)), st);
       k_place_hubs<<<nblk(m_hub), BS, 0, st>>>(ids, m_hub, bTc, 0, R.row_order, act);
       CK_LAUNCH();
       bTc -= m_hub;
     }
     if (n_hub > 0) {
-      int64_t c = compact(m, n, nullptr, 0, deg, int32_t(m), 1);
+      int64_t c = compact(m, n, nullptr, 0, deg, int32_t(m), 1, nF);
       radix_sort_pairs(keys, ids, c, bits_for(uint64_t(m)), st);
       k_place_hubs<<<nblk(n_hub), BS, 0, st>>>(ids, n_hub, bFc, m, R.col_order, act);
       CK_LAUNCH();
@@ -390,17 +396,18 @@ void run_reorder(fastpi_ctx* h, double k, Reordering& R) {
     CK(cudaMemsetAsync(cntT.get(), 0, size_t(N) * 4, st));
     CK(cudaMemsetAsync(cntF.get(), 0, size_t(N) * 4, st));
     CK(cudaMemsetAsync(best.get(), 0, 8, st));
+    CK(cudaMemsetAsync(dnroots.get(), 0, 4, st));
     if (nnz > 0) {
       k_cc_hook<<<nblk(nnz), BS, 0, st>>>(nz_row, h->col, act, m, nnz, parent, h->dstatus);
       CK_LAUNCH();
     }
     k_cc_label<<<nblk(N), BS, 0, st>>>(act, N, parent, label, m, cntT, cntF);
     CK_LAUNCH();
-    k_gcc<<<nblk(N), BS, 0, st>>>(act, label, cntT, cntF, N, best);
+    k_gcc<<<nblk(N), BS, 0, st>>>(act, label, cntT, cntF, N, best, dnroots);
     CK_LAUNCH();
-    k_summary<<<1, 1, 0, st>>>(best, cntT, cntF, summ);
+    k_summary<<<1, 1, 0, st>>>(best, cntT, cntF, dnroots, summ);
     CK_LAUNCH();
-    int64_t sm[3];
+    int64_t sm[4];
     d2h_sync(sm, summ, sizeof sm, st);
     gcc = int32_t(sm[0]);
     if (gcc < 0) {   // G' is empty
@@ -408,27 +415,28 @@ void run_reorder(fastpi_ctx* h, double k, Reordering& R) {
       break;
     }
     // non-giant components: front positions in (label asc, id asc)
-    int64_t cT = compact(0, m, label, gcc, label, 0, 0);
+    // rows of the non-giant components: the active rows less the hubs just
+    // placed and the GCC's rows (likewise for the features)
+    int64_t cT = compact(0, m, label, gcc, label, 0, 0, nI - m_hub - sm[1]);
     if (cT > 0) {
       radix_sort_pairs(keys, ids, cT, bits_for(uint64_t(N)), st);
       k_place_front<<<nblk(cT), BS, 0, st>>>(ids, cT, fT, R.row_order);
       CK_LAUNCH();
     }
-    int64_t cF = compact(m, n, label, gcc, label, 0, 0);
+    int64_t cF = compact(m, n, label, gcc, label, 0, 0, nF - n_hub - sm[2]);
     if (cF > 0) {
       radix_sort_pairs(keys, ids, cF, bits_for(uint64_t(N)), st);
       k_place_front<<<nblk(cF), BS, 0, st>>>(ids, cF, fF, R.col_order);
       CK_LAUNCH();
     }
     // one block per non-giant component, in ascending label (= root id) order
-    k_flags_roots<<<nblk(N), BS, 0, st>>>(act, label, gcc, N, flags);
-    CK_LAUNCH();
-    exclusive_scan_i32(flags, pos, N, st);
-    k_compact<<<nblk(N), BS, 0, st>>>(flags, pos, N, nullptr, 0, 0, 0, ids, nullptr, dcount);
-    CK_LAUNCH();
-    int32_t nroots = 0;
-    d2h_sync(&nroots, dcount, 4, st);
+    const int64_t nroots = sm[3];
     if (nroots > 0) {
+      k_flags_roots<<<nblk(N), BS, 0, st>>>(act, label, gcc, N, flags);
+      CK_LAUNCH();
+      exclusive_scan_i32(flags, pos, N, st);
+      k_compact<<<nblk(N), BS, 0, st>>>(flags, pos, N, nullptr, 0, 0, 0, ids, nullptr, dcount);
+      CK_LAUNCH();
       k_block_counts<<<nblk(nroots), BS, 0, st>>>(ids, nroots, cntT, cntF, bT, bF);
       CK_LAUNCH();
       exclusive_scan_i64(bT, bT, nroots, st);
@@ -449,13 +457,13 @@ void run_reorder(fastpi_ctx* h, double k, Reordering& R) {
   }
   // the final GCC fills the middle positions and forms the last A11 block
   if (nI + nF > 0) {
-    int64_t c = compact(0, m, nullptr, 0, nullptr, 0, 0);
+    int64_t c = compact(0, m, nullptr, 0, nullptr, 0, 0, nI);
     if (c > 0) {
       k_place_front<<<nblk(c), BS, 0, st>>>(ids, c, fT, R.row_order);
       CK_LAUNCH();
     }
     fT += c;
-    int64_t c2 = compact(m, n, nullptr, 0, nullptr, 0, 0);
+    int64_t c2 = compact(m, n, nullptr, 0, nullptr, 0, 0, nF);
     if (c2 > 0) {
       k_place_front<<<nblk(c2), BS, 0, st>>>(ids, c2, fF, R.col_order);
       CK_LAUNCH();
