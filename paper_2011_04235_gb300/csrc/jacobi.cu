@@ -393,6 +393,11 @@ __global__ void k_colnorms(const T* __restrict__ A, int64_t lda, int p, int q, d
   if (lane == 0) out[j] = sqrt(s);
 }
 
+// FP32 problems with at least ROUTE_MIN_Q columns, the ROUTE_MAX largest,
+// run in the cluster form of block Jacobi instead of a bucket.
+constexpr int ROUTE_MIN_Q = 96;
+constexpr int ROUTE_MAX = 16;
+
 template <typename T> struct Eps;
 template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; };
 template <> struct Eps<float> { static constexpr double v = 1.1920928955078125e-07; };
@@ -580,8 +585,47 @@ JacobiStats jacobi_svd_batched(fastpi_ctx* h, const std::vector<JacobiProblem<T>
   constexpr int NCLASS = 5;
   std::vector<JacobiProblem<T>> bucket[NCLASS];
   std::vector<int64_t> off[NCLASS];
+  std::vector<char> routed(nprob, 0);
+  if constexpr (sizeof(T) == 4) {
+    // The largest FP32 problems go one by one to the cluster form of block
+    // Jacobi: in a bucket a problem with q columns costs q - 1 device-wide
+    // barriers per sweep (and sets the pace of every problem in its bucket),
+    // in the cluster form about q / 8 rounds of one cluster each.
+    std::vector<int> cand;
+    for (int b = 0; b < nprob; ++b)
+      if (probs[b].q >= ROUTE_MIN_Q && probs[b].p >= probs[b].q && probs[b].lda == probs[b].p &&
+          probs[b].ldv == probs[b].q)
+        cand.push_back(b);
+    std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) { return probs[a].q > probs[b].q; });
+    if (int(cand.size()) > ROUTE_MAX) cand.resize(ROUTE_MAX);
+    std::vector<int64_t> offs(nprob, 0);
+    for (int b = 1; b < nprob; ++b) offs[b] = offs[b - 1] + probs[b - 1].q;
+    for (int b : cand) {
+      const JacobiProblem<T>& P = probs[b];
+      CoreTiling tl;
+      tuned_core_tiling(P.q, &tl);
+      JacobiStats js;
+      float ms = 0;
+      int sw = 0;
+      bool res = false;
+      if (!jacobi_svd_cluster(h, reinterpret_cast<float*>(P.A), P.lda, reinterpret_cast<float*>(P.V), P.ldv, P.p,
+                              P.q, tl, &js, &ms, &sw, &res))
+        continue;   // stays in its bucket
+      std::vector<JacobiProblem<T>> one(1, P);
+      jacobi_sort_columns<T>(h, one, sig + offs[b], perm + offs[b]);
+      routed[b] = 1;
+      stats.max_sweeps_used = std::max(stats.max_sweeps_used, js.max_sweeps_used);
+      stats.hit_cap = stats.hit_cap || js.hit_cap;
+      const double p = P.p, q = P.q;
+      note_svd(kind, ms, 4 * p * q * q + 8 * q * q * q, double(sw) * (q * (q - 1) / 2) * (12 * p + 6 * q));
+    }
+  }
   int64_t soff = 0;
   for (int b = 0; b < nprob; ++b) {
+    if (routed[b]) {
+      soff += probs[b].q;
+      continue;
+    }
     const int c = tuned_bucket_class(sizeof(T) == 8 ? 0 : 1, std::max(probs[b].p, probs[b].q),
                                      tile_class<T>(probs[b]));
     bucket[c].push_back(probs[b]);

@@ -67,11 +67,13 @@ struct CoreTiling {
 // for the outputs of jacobi_svd_block (n x n column-major, ld n).
 void core_vectors_f32(fastpi_ctx* h, int n, const float* K, const float* V, const double* sig, const int32_t* perm,
                       float* U, float* Vs);
-// The cluster form of the block Jacobi core SVD (jacobi_cluster.cu): K <- K J
-// and V <- J (n x n, column-major, ld n) as jacobi_svd_block computes them,
-// before the final sort.  false, having done nothing, when the tiling does not
-// fit (shared memory, co-resident clusters) or the launch form is refused.
-bool jacobi_svd_cluster(fastpi_ctx* h, float* K, float* V, int n, const CoreTiling& tiling, JacobiStats* stats,
-                        float* ms, int* sweeps, bool* used_res);
+// The cluster form of block one-sided Jacobi (jacobi_cluster.cu) on a p x n
+// FP32 problem (p >= n, column-major, ld lda): K <- K J with mutually
+// orthogonal columns and V (n x n, ld ldv) <- J, as jacobi_svd_block computes
+// them before the final sort.  false, having done nothing, when the tiling
+// does not fit (shared memory, co-resident clusters) or the launch form is
+// refused.
+bool jacobi_svd_cluster(fastpi_ctx* h, float* K, int64_t lda, float* V, int64_t ldv, int p, int n,
+                        const CoreTiling& tiling, JacobiStats* stats, float* ms, int* sweeps, bool* used_res);
 
 }  // namespace fastpi

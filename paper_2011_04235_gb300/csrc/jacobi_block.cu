@@ -404,23 +404,24 @@ __global__ void k_b_sumsq_final(const double* part, int np, BBar* gb) {
   }
 }
 
-// Kp (ldk x n) <- K (n x n, ld n) with zero rows n..ldk-1; Vp <- I (ldk x n).
-__global__ void k_b_pad_in(const float* __restrict__ K, int n, int ldk, float* __restrict__ Kp,
+// Kp (ldk x q) <- K (p x q, ld lda) with zero rows p..ldk-1; Vp <- I (ldk x q).
+__global__ void k_b_pad_in(const float* __restrict__ K, int64_t lda, int p, int q, int ldk, float* __restrict__ Kp,
                            float* __restrict__ Vp) {
   const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (e >= int64_t(ldk) * n) return;
+  if (e >= int64_t(ldk) * q) return;
   const int c = int(e / ldk), r = int(e % ldk);
-  Kp[e] = r < n ? K[int64_t(c) * n + r] : 0.f;
+  Kp[e] = r < p ? K[int64_t(c) * lda + r] : 0.f;
   Vp[e] = r == c ? 1.f : 0.f;
 }
-// K (n x n) <- Kp, V (n x n) <- Vp.
-__global__ void k_b_pad_out(const float* __restrict__ Kp, const float* __restrict__ Vp, int n, int ldk,
-                            float* __restrict__ K, float* __restrict__ V) {
+// K (p x q, ld lda) <- Kp, V (q x q, ld ldv) <- Vp.
+__global__ void k_b_pad_out(const float* __restrict__ Kp, const float* __restrict__ Vp, int p, int q, int ldk,
+                            float* __restrict__ K, int64_t lda, float* __restrict__ V, int64_t ldv) {
   const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (e >= int64_t(n) * n) return;
-  const int c = int(e / n), r = int(e % n);
-  K[e] = Kp[int64_t(c) * ldk + r];
-  V[e] = Vp[int64_t(c) * ldk + r];
+  const int rows = p > q ? p : q;
+  if (e >= int64_t(rows) * q) return;
+  const int c = int(e / rows), r = int(e % rows);
+  if (r < p) K[int64_t(c) * lda + r] = Kp[int64_t(c) * ldk + r];
+  if (r < q) V[int64_t(c) * ldv + r] = Vp[int64_t(c) * ldk + r];
 }
 
 // FASTPI_JACOBI_RESIDENT=1 selects the resident-block schedule (same pairs,
@@ -465,7 +466,7 @@ bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats,
   DArr<int> out(2, st);
   DArr<unsigned> ver(int64_t(nb) * VER_STRIDE, st);
   DArr<float> Kp(int64_t(ldk) * n, st), Vp(int64_t(ldk) * n, st);
-  core_prepare(hc, K, n, ldk, Kp.get(), Vp.get(), part.get(), NPART, gb.get());
+  core_prepare(hc, K, n, n, n, ldk, Kp.get(), Vp.get(), part.get(), NPART, gb.get());
   CK(cudaMemsetAsync(out.get(), 0, 2 * sizeof(int), st));
   CK(cudaMemsetAsync(ver.get(), 0, size_t(nb) * VER_STRIDE * sizeof(unsigned), st));
   CK(cudaMemsetAsync(hc->dstatus.get(), 0, 4, st));
@@ -490,7 +491,7 @@ bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats,
   CK(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(BT), args, smem, st));
   CK_LAUNCH();
   CK(cudaEventRecord(ev1, st));
-  core_finish(hc, Kp.get(), Vp.get(), n, ldk, K, V);
+  core_finish(hc, Kp.get(), Vp.get(), n, n, ldk, K, n, V, n);
   int ho[2] = {0, 0};
   d2h_sync(ho, out.get(), sizeof ho, st);
   unsigned stat = 0;
@@ -528,19 +529,22 @@ bool launch_block(fastpi_ctx* hc, float* K, float* V, int n, JacobiStats* stats,
 
 namespace jdev {
 
-void core_prepare(fastpi_ctx* hc, const float* K, int n, int ldk, float* Kp, float* Vp, double* part, int npart,
-                  BBar* gb) {
+void core_prepare(fastpi_ctx* hc, const float* K, int64_t lda, int p, int q, int ldk, float* Kp, float* Vp,
+                  double* part, int npart, BBar* gb) {
   cudaStream_t st = hc->stream;
-  k_b_sumsq_part<<<npart, 256, 0, st>>>(K, int64_t(n) * n, part);
+  // |K|_F^2 over the p x q entries (K packed: lda == p, or a square core)
+  k_b_sumsq_part<<<npart, 256, 0, st>>>(K, int64_t(lda) * q, part);
   CK_LAUNCH();
   k_b_sumsq_final<<<1, 32, 0, st>>>(part, npart, gb);
   CK_LAUNCH();
-  k_b_pad_in<<<unsigned((int64_t(ldk) * n + 255) / 256), 256, 0, st>>>(K, n, ldk, Kp, Vp);
+  k_b_pad_in<<<unsigned((int64_t(ldk) * q + 255) / 256), 256, 0, st>>>(K, lda, p, q, ldk, Kp, Vp);
   CK_LAUNCH();
 }
 
-void core_finish(fastpi_ctx* hc, const float* Kp, const float* Vp, int n, int ldk, float* K, float* V) {
-  k_b_pad_out<<<unsigned((int64_t(n) * n + 255) / 256), 256, 0, hc->stream>>>(Kp, Vp, n, ldk, K, V);
+void core_finish(fastpi_ctx* hc, const float* Kp, const float* Vp, int p, int q, int ldk, float* K, int64_t lda,
+                 float* V, int64_t ldv) {
+  const int rows = p > q ? p : q;
+  k_b_pad_out<<<unsigned((int64_t(rows) * q + 255) / 256), 256, 0, hc->stream>>>(Kp, Vp, p, q, ldk, K, lda, V, ldv);
   CK_LAUNCH();
 }
 
@@ -585,7 +589,7 @@ bool jacobi_svd_block(fastpi_ctx* hc, float* K, float* V, int n, double* sig, in
     }
     if (std::getenv("FASTPI_JACOBI_RESIDENT")) tl.resident = resident_schedule();
   }
-  if (!tl.single_cta) ok = jacobi_svd_cluster(hc, K, V, n, tl, stats, &ms, &sweeps, &res);
+  if (!tl.single_cta) ok = jacobi_svd_cluster(hc, K, n, V, n, n, n, tl, stats, &ms, &sweeps, &res);
   if (!ok && !(tl.strict && !tl.single_cta)) {
     // the single-CTA kernel (its resident form from the environment only)
     ok = launch_block<16, true>(hc, K, V, n, stats, &ms, &sweeps, &res);

@@ -50,10 +50,11 @@ constexpr int CT = 256;                 // threads per CTA (8 warps)
 constexpr int C_MAX_SWEEPS = 30;
 
 struct ClArgs {
-  float* K;         // ldk x n column-major: in A (rows >= n zero), out A J
+  float* K;         // ldk x n column-major: in A (rows >= its row count zero), out A J
   float* V;         // ldk x n column-major: in I, out J
   unsigned* ver;    // [nb * C * VER_STRIDE]: rounds completed per (block, row part)
-  int n, ldk, rpc;  // ldk = C * rpc; rpc a multiple of 4
+  int n, ldk, rpc;  // n columns; ldk = C * rpc rows (>= the row count); rpc a multiple of 4
+  int len;          // the longer side of the problem (the absolute zero threshold scales with it)
   int nb;           // number of column blocks (even)
   int parts;        // C: CTAs per cluster the grid was laid out for
   float tol;
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(CT) k_jacobi_cluster(ClArgs a) {
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float tabs = [&] {
-    const float ne = float(n) * 1.1920929e-7f;
+    const float ne = float(a.len) * 1.1920929e-7f;
     return float(double(ne) * double(ne) * a.gb->fro2);
   }();
   const float tol2 = a.tol * a.tol, early2 = a.early * a.early;
@@ -417,8 +418,8 @@ int pick_parts(int slots, int num_sms, int want) {
 }
 
 template <int P, bool RES, bool FAST>
-bool launch_cluster(fastpi_ctx* hc, float* K, float* V, int n, int parts, float early, JacobiStats* stats,
-                    float* ms_out, int* sweeps) {
+bool launch_cluster(fastpi_ctx* hc, float* K, int64_t lda, float* V, int64_t ldv, int p, int n, int parts,
+                    float early, JacobiStats* stats, float* ms_out, int* sweeps) {
   cudaStream_t st = hc->stream;
   constexpr int B = P / 2;
   int nb = (n + B - 1) / B;
@@ -426,7 +427,8 @@ bool launch_cluster(fastpi_ctx* hc, float* K, float* V, int n, int parts, float 
   if (nb < 2) nb = 2;
   const int slots = nb / 2;
   const int C = parts;
-  int rpc = (n + C - 1) / C;
+  const int len = std::max(p, n);
+  int rpc = (len + C - 1) / C;
   rpc = (rpc + 3) / 4 * 4;
   const int ldk = C * rpc;
   const size_t smem = cluster_smem(P, C, rpc);
@@ -472,7 +474,7 @@ bool launch_cluster(fastpi_ctx* hc, float* K, float* V, int n, int parts, float 
   DArr<int> out(2, st);
   DArr<unsigned> ver(int64_t(nb) * C * VER_STRIDE, st);
   DArr<float> Kp(int64_t(ldk) * n, st), Vp(int64_t(ldk) * n, st);
-  core_prepare(hc, K, n, ldk, Kp.get(), Vp.get(), partsum.get(), NPART, gb.get());
+  core_prepare(hc, K, lda, p, n, ldk, Kp.get(), Vp.get(), partsum.get(), NPART, gb.get());
   CK(cudaMemsetAsync(out.get(), 0, 2 * sizeof(int), st));
   CK(cudaMemsetAsync(ver.get(), 0, size_t(nb) * C * VER_STRIDE * sizeof(unsigned), st));
   CK(cudaMemsetAsync(hc->dstatus.get(), 0, 4, st));
@@ -482,11 +484,12 @@ bool launch_cluster(fastpi_ctx* hc, float* K, float* V, int n, int parts, float 
   a.V = Vp.get();
   a.ver = ver.get();
   a.n = n;
+  a.len = len;
   a.ldk = ldk;
   a.rpc = rpc;
   a.nb = nb;
   a.parts = C;
-  a.tol = float(std::sqrt(double(n)) * 1.1920928955078125e-07);
+  a.tol = float(std::sqrt(double(len)) * 1.1920928955078125e-07);
   a.early = early;
   a.gb = gb.get();
   a.out = out.get();
@@ -506,7 +509,7 @@ bool launch_cluster(fastpi_ctx* hc, float* K, float* V, int n, int parts, float 
   }
   CK_LAUNCH();
   CK(cudaEventRecord(ev1, st));
-  core_finish(hc, Kp.get(), Vp.get(), n, ldk, K, V);
+  core_finish(hc, Kp.get(), Vp.get(), p, n, ldk, K, lda, V, ldv);
   int ho[2] = {0, 0};
   d2h_sync(ho, out.get(), sizeof ho, st);
   unsigned stat = 0;
@@ -547,15 +550,16 @@ bool launch_cluster(fastpi_ctx* hc, float* K, float* V, int n, int parts, float 
 
 }  // namespace
 
-bool jacobi_svd_cluster(fastpi_ctx* hc, float* K, float* V, int n, const CoreTiling& tiling, JacobiStats* stats,
-                        float* ms, int* sweeps, bool* used_res) {
+bool jacobi_svd_cluster(fastpi_ctx* hc, float* K, int64_t lda, float* V, int64_t ldv, int p, int n,
+                        const CoreTiling& tiling, JacobiStats* stats, float* ms, int* sweeps, bool* used_res) {
   const int P = tiling.panel;
   const int B = P / 2;
   int nb = (n + B - 1) / B;
   if (nb & 1) ++nb;
   const int C = pick_parts(std::max(nb / 2, 1), hc->num_sms, tiling.parts);
   *used_res = tiling.resident;
-#define FASTPI_CL(PV, RV, WV) launch_cluster<PV, RV, WV>(hc, K, V, n, C, tiling.early_exit, stats, ms, sweeps)
+#define FASTPI_CL(PV, RV, WV) \
+  launch_cluster<PV, RV, WV>(hc, K, lda, V, ldv, p, n, C, tiling.early_exit, stats, ms, sweeps)
   const bool r = tiling.resident, w = tiling.fast_solve;
   if (P == 16) return r ? (w ? FASTPI_CL(16, true, true) : FASTPI_CL(16, true, false))
                         : (w ? FASTPI_CL(16, false, true) : FASTPI_CL(16, false, false));

@@ -334,12 +334,14 @@ __device__ __forceinline__ float* ns_orthonormalize(const float* Q, float* W, fl
 }
 
 // Host side, shared by the two core kernels (defined in jacobi_block.cu):
-// Kp (ldk x n, column-major) <- K (n x n, ld n) with zero rows n..ldk-1,
-// Vp <- I; gb->fro2 = |K|_F^2 (fixed-order sum) and the barrier reset.
-void core_prepare(fastpi_ctx* hc, const float* K, int n, int ldk, float* Kp, float* Vp, double* part, int npart,
-                  BBar* gb);
-// K (n x n) <- Kp, V (n x n) <- Vp.
-void core_finish(fastpi_ctx* hc, const float* Kp, const float* Vp, int n, int ldk, float* K, float* V);
+// Kp (ldk x q, column-major) <- K (p x q, ld lda; lda == p or a square core)
+// with zero rows p..ldk-1, Vp <- I (ldk x q); gb->fro2 = |K|_F^2 (fixed-order
+// sum) and the barrier reset.
+void core_prepare(fastpi_ctx* hc, const float* K, int64_t lda, int p, int q, int ldk, float* Kp, float* Vp,
+                  double* part, int npart, BBar* gb);
+// K (p x q, ld lda) <- Kp, V (q x q, ld ldv) <- Vp.
+void core_finish(fastpi_ctx* hc, const float* Kp, const float* Vp, int p, int q, int ldk, float* K, int64_t lda,
+                 float* V, int64_t ldv);
 
 }  // namespace jdev
 }  // namespace fastpi
