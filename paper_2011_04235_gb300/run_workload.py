@@ -12,6 +12,8 @@ The many-instance workload (independent matrices, m log-uniform in
 instance after another and through fastpi_factor_batched:
 
   python -m paper_2011_04235_gb300.run_workload many [count] [precision] [concurrency[,concurrency...]]
+
+(concurrency 0: the one-after-another pass only).
 """
 from __future__ import annotations
 
@@ -55,8 +57,8 @@ def run_many(count: int, prec: str, concurrency: list):
         seq_res[i] = h.residual(Y, h.apply(Y))
         h.close()
 
-    # batched: one stream per instance, for each requested concurrency
-    for conc in concurrency:
+    # batched: one stream per instance, for each requested concurrency (0: none)
+    for conc in (c for c in concurrency if c > 0):
         hs = [fastpi.FastPI(w["m"], w["n"], *c, device=dev, stream=s.cuda_stream)
               for w, c, s in zip(ws, csr, streams)]
         torch.cuda.synchronize()
