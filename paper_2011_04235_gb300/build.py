@@ -7,10 +7,12 @@ _build/, then linked into paper_2011_04235_gb300/libfastpi.so (CUDA runtime
 linked statically).  An object is rebuilt only when its source or a header
 changed, or when the compile flags differ from those of the last build.
 
---phase-clocks builds the instrumented core SVD: the block Jacobi kernel
-accumulates clock64() per phase of a round (wait, load, Gram, solve, update)
-in one CTA and prints the per-round averages to stderr after each launch.  It
-is a measurement build only; build again without the flag afterwards.
+--phase-clocks builds the instrumented kernels: the block Jacobi kernels
+accumulate clock64() per phase of a round (wait, load, Gram, solve, update)
+in one CTA and print the per-round averages to stderr after each launch; the
+pivoted-Cholesky panel kernel accumulates its clocks per step and prints them
+after each factorization.  It is a measurement build only; build again
+without the flag afterwards.
 """
 from __future__ import annotations
 

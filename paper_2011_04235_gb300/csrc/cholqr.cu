@@ -14,20 +14,64 @@ namespace {
 
 constexpr int NB = 32;   // block edge
 
-// In shared memory, by one warp (lane j = column j): Linv = inverse of the
-// lower-triangular NB x NB block Lb (row stride NB + 1) restricted to the
+// By one warp (lane j = column j): Linv = inverse of the lower-triangular
+// NB x NB block Lb (shared memory, row stride NB + 1) restricted to the
 // indices with keep[i] != 0 (zero rows and columns elsewhere), by forward
-// substitution; bs = rows / columns in use.
+// substitution with the column held in registers (unrolled: the loads of Lb
+// are broadcasts independent of the running sums, so only the multiply-add
+// chain of each row is serial); bs = rows / columns in use.
 template <typename T>
 __device__ __forceinline__ void warp_trinv_block(const T* Lb, const int* keep, int bs, int lane, T* Linv) {
   const int j = lane;
   const bool colk = j < bs && keep[j];
+  T x[NB];
+#pragma unroll
   for (int i = 0; i < NB; ++i) {
     T s = (i == j) ? T(1) : T(0);
-    for (int l = j; l < i; ++l) s = fma(-Lb[i * (NB + 1) + l], Linv[l * (NB + 1) + j], s);
-    Linv[i * (NB + 1) + j] = (colk && i < bs && keep[i] && i >= j) ? s / Lb[i * (NB + 1) + i] : T(0);
-    __syncwarp();
+    // x[l] = 0 for l < j, so the sum is the one over l = j .. i-1
+#pragma unroll
+    for (int l = 0; l < i; ++l) s = fma(-Lb[i * (NB + 1) + l], x[l], s);
+    x[i] = (colk && i < bs && keep[i] && i >= j) ? s / Lb[i * (NB + 1) + i] : T(0);
   }
+#pragma unroll
+  for (int i = 0; i < NB; ++i) Linv[i * (NB + 1) + j] = x[i];
+  __syncwarp();
+}
+
+// By one warp: Cholesky of the symmetric NB x NB block Ab (shared memory, row
+// stride NB + 1, lower triangle used) in place, columns j < bw, with the drop
+// rule (a pivot d_j <= tol gives a zero column); lane l holds row l in
+// registers and takes the entries of other rows by warp shuffles.  Returns
+// the bit mask of kept columns.
+__device__ __forceinline__ unsigned warp_chol_block(float* Ab, int bw, float tol, int lane) {
+  float a[NB];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) a[i] = (i <= lane && lane < bw && i < bw) ? Ab[lane * (NB + 1) + i] : 0.f;
+  unsigned keepmask = 0;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    const float d = __shfl_sync(0xffffffffu, a[j], j);
+    const bool keep = j < bw && d > tol;
+    const float ljj = keep ? sqrtf(d) : 0.f;
+    const float inv = keep ? 1.f / ljj : 0.f;
+    if (lane == j)
+      a[j] = ljj;
+    else if (lane > j)
+      a[j] *= inv;
+    if (keep) {
+      keepmask |= 1u << j;
+#pragma unroll
+      for (int i = j + 1; i < NB; ++i) {
+        const float lij = __shfl_sync(0xffffffffu, a[j], i);   // L[i, j]
+        if (lane >= i) a[i] = fmaf(-a[j], lij, a[i]);
+      }
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < NB; ++i) Ab[lane * (NB + 1) + i] = (i <= lane && lane < bw) ? a[i] : 0.f;
+  __syncwarp();
+  return keepmask;
 }
 
 // Dinv (nb blocks of NB x NB, row-major) <- inverse of each diagonal block of
@@ -54,43 +98,61 @@ __global__ void k_trinv_diag(const T* __restrict__ L, int c, const int32_t* __re
 // X (c x c, row-major) <- L^-1 restricted to the kept indices, one CTA per
 // block column jb: X_jj = Dinv_j and, block row after block row,
 // X_ij = -Dinv_i (sum_{k = j .. i-1} L_ik X_kj); the block column of X stays in
-// shared memory.  Entries above the diagonal are zero.
+// shared memory, and L_ik is staged through shared memory TI_KC columns at a
+// time (coalesced copies instead of a chain of dependent L2 loads per dot
+// product).  Entries above the diagonal are zero.  256 threads: thread
+// (warp w, lane s) owns the entries (w + 8 q, s), q = 0..3, of a block.
+constexpr int TI_KC = 64;
+constexpr int TI_THREADS = 256;
 template <typename T>
-__global__ void __launch_bounds__(256) k_trinv_cols_blocked(const T* __restrict__ L, int c,
-                                                            const T* __restrict__ Dinv, T* __restrict__ X) {
+__global__ void __launch_bounds__(TI_THREADS) k_trinv_cols_blocked(const T* __restrict__ L, int c,
+                                                                   const T* __restrict__ Dinv, T* __restrict__ X) {
   extern __shared__ unsigned char xs_raw[];
   const int nb = (c + NB - 1) / NB, jb = blockIdx.x, tid = threadIdx.x;
+  const int w = tid >> 5, lane = tid & 31;
   T* Xc = reinterpret_cast<T*>(xs_raw);          // [nb * NB][NB]: block column jb of X
   T* Tb = Xc + int64_t(nb) * NB * NB;            // [NB][NB] scratch
-  const int c0 = jb * NB, bw = min(NB, c - c0);
-  for (int e = tid; e < nb * NB * NB; e += blockDim.x) Xc[e] = T(0);
+  T* Ls = Tb + NB * NB;                          // [NB][TI_KC]: staged columns of L's block row
+  T* Ds = Ls + NB * TI_KC;                       // [NB][NB]: Dinv of the block row
+  const int c0 = jb * NB;
+  for (int e = tid; e < nb * NB * NB; e += TI_THREADS) Xc[e] = T(0);
   __syncthreads();
-  for (int e = tid; e < NB * NB; e += blockDim.x) Xc[int64_t(jb) * NB * NB + e] = Dinv[int64_t(jb) * NB * NB + e];
+  for (int e = tid; e < NB * NB; e += TI_THREADS) Xc[int64_t(jb) * NB * NB + e] = Dinv[int64_t(jb) * NB * NB + e];
   __syncthreads();
   for (int ib = jb + 1; ib < nb; ++ib) {
     const int r0 = ib * NB, bh = min(NB, c - r0);
+    for (int e = tid; e < NB * NB; e += TI_THREADS) Ds[e] = Dinv[int64_t(ib) * NB * NB + e];
     // T = sum over the block rows jb .. ib-1 of L[ib, k] X[k, jb]
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-      const int r = e / NB, s = e % NB;
-      T acc = T(0);
-      if (r < bh && s < bw) {
-        const T* Lr = L + int64_t(r0 + r) * c;
-        for (int k = c0; k < r0; ++k) acc = fma(__ldcg(Lr + k), Xc[int64_t(k) * NB + s], acc);
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    for (int k0 = c0; k0 < r0; k0 += TI_KC) {
+      const int kc = min(TI_KC, r0 - k0);
+      for (int e = tid; e < NB * TI_KC; e += TI_THREADS) {
+        const int r = e / TI_KC, k = e % TI_KC;
+        Ls[e] = (r < bh && k < kc) ? L[int64_t(r0 + r) * c + k0 + k] : T(0);
       }
-      Tb[e] = acc;
+      __syncthreads();
+      for (int k = 0; k < kc; ++k) {
+        const T x = Xc[int64_t(k0 + k) * NB + lane];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = fma(Ls[(w + 8 * q) * TI_KC + k], x, acc[q]);
+      }
+      __syncthreads();
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Tb[(w + 8 * q) * NB + lane] = acc[q];
     __syncthreads();
     // X[ib, jb] = -Dinv_ib T
-    const T* Di = Dinv + int64_t(ib) * NB * NB;
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-      const int r = e / NB, s = e % NB;
-      T acc = T(0);
-      for (int k = 0; k < NB; ++k) acc = fma(__ldcg(Di + r * NB + k), Tb[k * NB + s], acc);
-      Xc[int64_t(r0 + r) * NB + s] = -acc;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = w + 8 * q;
+      T o = T(0);
+      for (int k = 0; k < NB; ++k) o = fma(Ds[r * NB + k], Tb[k * NB + lane], o);
+      Xc[int64_t(r0 + r) * NB + lane] = -o;
     }
     __syncthreads();
   }
-  for (int e = tid; e < c * NB; e += blockDim.x) {
+  const int bw = min(NB, c - c0);
+  for (int e = tid; e < c * NB; e += TI_THREADS) {
     const int r = e / NB, s = e % NB;
     if (s < bw) X[int64_t(r) * c + c0 + s] = Xc[e];
   }
@@ -125,25 +187,9 @@ __global__ void __launch_bounds__(1024) k_chol_drop_blocked(float* G, int c, flo
     if (warp == 0) {
       for (int i = 0; i < NB; ++i) Ab[i * (NB + 1) + lane] = (i < bw && lane <= i) ? Pk[pk(k0 + i, k0 + lane)] : 0.f;
       __syncwarp();
-      int nk = 0;
-      for (int j = 0; j < bw; ++j) {
-        const float d = Ab[j * (NB + 1) + j];
-        const bool keep = d > tol;
-        const float ljj = keep ? sqrtf(d) : 0.f;
-        const float inv = keep ? 1.f / ljj : 0.f;
-        __syncwarp();
-        if (lane == j) Ab[j * (NB + 1) + j] = ljj;
-        if (lane > j && lane < bw) Ab[lane * (NB + 1) + j] *= inv;
-        __syncwarp();
-        if (keep && lane > j && lane < bw) {
-          const float lij = Ab[lane * (NB + 1) + j];
-          for (int l = j + 1; l <= lane; ++l) Ab[lane * (NB + 1) + l] -= lij * Ab[l * (NB + 1) + j];
-        }
-        if (lane == 0) s_keep[j] = keep ? 1 : 0;
-        nk += keep ? 1 : 0;
-        __syncwarp();
-      }
-      if (lane == 0) s_nk += nk;
+      const unsigned km = warp_chol_block(Ab, bw, tol, lane);
+      s_keep[lane] = int((km >> lane) & 1u);
+      if (lane == 0) s_nk += __popc(km);
       __syncwarp();
       warp_trinv_block<float>(Ab, s_keep, bw, lane, Ai);
       for (int i = 0; i < bw; ++i)
@@ -223,13 +269,13 @@ void trinv_blocked(cudaStream_t st, const T* L, int c, const int32_t* kept, T* X
   CK_LAUNCH();
   const size_t smem = trinv_blocked_smem(c, sizeof(T));
   if (smem > 48 * 1024) allow_max_dynamic_smem((const void*)k_trinv_cols_blocked<T>);
-  k_trinv_cols_blocked<T><<<unsigned(nb), 256, smem, st>>>(L, c, Dinv.get(), X);
+  k_trinv_cols_blocked<T><<<unsigned(nb), TI_THREADS, smem, st>>>(L, c, Dinv.get(), X);
   CK_LAUNCH();
 }
 
 size_t trinv_blocked_smem(int c, size_t elem) {
   const int nb = (c + NB - 1) / NB;
-  return (size_t(nb) * NB * NB + NB * NB) * elem;
+  return (size_t(nb) * NB * NB + 2 * NB * NB + NB * TI_KC) * elem;
 }
 
 size_t chol_drop_blocked_smem(int c) { return size_t(int64_t(c) * (c + 1) / 2) * sizeof(float); }

@@ -374,15 +374,64 @@ __global__ void k_pchol(const double* G, int c, const double* dn, double tol, do
 // that turns R (p x c) into Q1 = R Linv_orig^T.
 // Blocked form of k_pchol.  G (c x c, FP64, full symmetric) holds the Schur
 // complement of the columns factored so far (earlier panels are removed from
-// it by a GEMM after each panel); d / used / Lo / piv / kept / rank persist in
-// global memory across the panels.  One CTA factors the panel columns
-// [t0, t0 + nb) with the same pivot rule and drop test as k_pchol: the pivot
-// is the unused column with the largest remaining diagonal (ties to the lower
-// index); when it is <= thr the factorization stops (state[0] = 1).  The
-// panel's columns of Lo are staged in shared memory.
+// it by k_pchol_trailing after each panel); d / used / Lo / piv / kept / rank
+// persist in global memory across the panels (Lo zero before the first).  One
+// CTA factors the panel columns [t0, t0 + nb) with the same pivot rule and
+// drop test as k_pchol: the pivot is the unused column with the largest
+// remaining diagonal (ties to the lower index); when it is <= thr the
+// factorization stops (state[0] = 1).  The panel's columns of Lo are staged
+// in shared memory.
+//
+// A step is a chain of dependent parts, so each is kept off GB300's slow FP64
+// pipe where it can be: the pivot search compares order-preserving integer
+// images of the FP64 diagonal with warp reductions (value descending, index
+// ascending; no FP64 compare), one thread takes the square root and the
+// reciprocal and hands them to the others, and the row update splits its dot
+// product over four independent accumulators, issued before the load of the
+// pivot's row of G that it ends with.
 constexpr int PCHOL_NB = 32;
 constexpr int PCHOL_PS = PCHOL_NB + 1;   // panel row stride: odd, so a warp's rows fall in different banks
 constexpr int PCHOL_THREADS = 256;
+#ifdef FASTPI_PHASE_CLOCKS
+// clock64 per phase of the panel kernel, thread 0: 0 set-up, 1 pivot search
+// (with the square root and reciprocal), 4 row update, 5 CTA barrier,
+// 6 write-back, 7 steps
+__device__ long long g_pc1_clk[8];
+#define PC1_MARK(k)                          \
+  do {                                       \
+    if (threadIdx.x == 0) {                  \
+      const long long t_ = clock64();        \
+      g_pc1_clk[k] += t_ - t_mark;           \
+      t_mark = t_;                           \
+    }                                        \
+  } while (0)
+#else
+#define PC1_MARK(k) \
+  do {              \
+  } while (0)
+#endif
+
+// An unsigned image of a double whose order is the order of the values
+// (non-NaN): the sign bit flipped for non-negative values, all bits flipped
+// for negative ones.
+__device__ __forceinline__ unsigned long long order_key(double v) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double order_value(unsigned long long k) {
+  return __longlong_as_double(static_cast<long long>((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
+// Within a warp: the largest key, ties to the lowest index (idx = UINT_MAX
+// for lanes without a candidate); every lane gets the result.
+__device__ __forceinline__ void warp_argmax_key(unsigned long long& key, unsigned& idx) {
+  const unsigned hi = unsigned(key >> 32), lo = unsigned(key);
+  const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+  idx = __reduce_min_sync(0xffffffffu, (hi == mhi && lo == mlo) ? idx : 0xffffffffu);
+  key = (static_cast<unsigned long long>(mhi) << 32) | mlo;
+}
+
 __global__ void __launch_bounds__(PCHOL_THREADS) k_pchol_panel(const double* __restrict__ G, int c, int t0,
                                                                const double* dn, double tol, double* d,
                                                                int32_t* used, double* Lo, int32_t* piv,
@@ -390,10 +439,14 @@ __global__ void __launch_bounds__(PCHOL_THREADS) k_pchol_panel(const double* __r
   extern __shared__ double pan[];   // c x PCHOL_PS: Lo[:, t0 + k]; then d_s[c]; then used_s[c]
   double* d_s = pan + size_t(c) * PCHOL_PS;
   int* used_s = reinterpret_cast<int*>(d_s + c);
+  __shared__ unsigned long long red_k[PCHOL_THREADS / 32];
+  __shared__ unsigned red_i[PCHOL_THREADS / 32];
   __shared__ double red_v[PCHOL_THREADS / 32];
-  __shared__ int red_i[PCHOL_THREADS / 32];
-  __shared__ double s_best, s_thr;
-  __shared__ int s_arg;
+  __shared__ double s_thr, s_ljj, s_rljj;
+  __shared__ int s_arg, s_stop;
+#ifdef FASTPI_PHASE_CLOCKS
+  long long t_mark = clock64();
+#endif
   if (state[0]) return;   // an earlier panel stopped the factorization
   const int nb = min(PCHOL_NB, c - t0);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -414,8 +467,6 @@ __global__ void __launch_bounds__(PCHOL_THREADS) k_pchol_panel(const double* __r
     }
     mx = fmax(mx, dn[i]);
   }
-  if (t0 == 0)
-    for (int64_t e = tid; e < int64_t(c) * c; e += PCHOL_THREADS) Lo[e] = 0.0;
   for (int e = tid; e < c * PCHOL_PS; e += PCHOL_THREADS) pan[e] = 0.0;
 #pragma unroll
   for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -428,60 +479,54 @@ __global__ void __launch_bounds__(PCHOL_THREADS) k_pchol_panel(const double* __r
   }
   __syncthreads();
   int stop = 0;
+  PC1_MARK(0);
   for (int k = 0; k < nb; ++k) {
     const int t = t0 + k;
     // pivot: the unused column with the largest remaining diagonal (ties: lower index)
-    double bv = -1.0;
-    int bi = c;
+    unsigned long long bk = 0;
+    unsigned bi = 0xffffffffu;
     for (int i = tid; i < c; i += PCHOL_THREADS)
-      if (!used_s[i] && (d_s[i] > bv || (d_s[i] == bv && i < bi))) {
-        bv = d_s[i];
-        bi = i;
+      if (!used_s[i]) {
+        const unsigned long long kk = order_key(d_s[i]);
+        if (bi == 0xffffffffu || kk > bk) {   // rows ascend per thread: ties keep the first
+          bk = kk;
+          bi = unsigned(i);
+        }
       }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > bv || (ov == bv && oi < bi)) {
-        bv = ov;
-        bi = oi;
-      }
-    }
+    warp_argmax_key(bk, bi);
     if (lane == 0) {
-      red_v[w] = bv;
+      red_k[w] = bk;
       red_i[w] = bi;
     }
     __syncthreads();
     if (w == 0) {
-      bv = lane < NW ? red_v[lane] : -1.0;
-      bi = lane < NW ? red_i[lane] : c;
-#pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > bv || (ov == bv && oi < bi)) {
-          bv = ov;
-          bi = oi;
-        }
-      }
+      bk = lane < NW ? red_k[lane] : 0ull;
+      bi = lane < NW ? red_i[lane] : 0xffffffffu;
+      warp_argmax_key(bk, bi);
       if (lane == 0) {
-        s_best = bv;
-        s_arg = bi;
+        const double best = order_value(bk);
+        const bool st = bi >= unsigned(c) || !(best > s_thr);
+        s_stop = st ? 1 : 0;
+        s_arg = int(bi);
+        if (!st) {
+          const double ljj = sqrt(best);
+          s_ljj = ljj;
+          // one reciprocal instead of a division per row
+          s_rljj = 1.0 / ljj;
+        }
       }
     }
     __syncthreads();
-    const double best = s_best;
-    const int j = s_arg;
-    if (!(best > s_thr) || j >= c) {
+    PC1_MARK(1);
+    if (s_stop) {
       stop = 1;
       break;
     }
-    const double ljj = sqrt(best);
-    // one reciprocal instead of a division per row (GB300's FP64 pipe runs at
-    // 1/64 of its FP32 rate, and an FP64 division is a sequence of FMAs)
-    const double rljj = 1.0 / ljj;
+    const int j = s_arg;
+    const double ljj = s_ljj, rljj = s_rljj;
     // column t for every unused row other than the pivot: the Schur complement
     // column of pivot j (row j of G, by symmetry) minus this panel's earlier columns
+    const double* pj = pan + j * PCHOL_PS;
     for (int i = tid; i < c; i += PCHOL_THREADS) {
       if (i == j) {
         pan[j * PCHOL_PS + k] = ljj;
@@ -489,9 +534,17 @@ __global__ void __launch_bounds__(PCHOL_THREADS) k_pchol_panel(const double* __r
         continue;
       }
       if (used_s[i]) continue;
-      double sacc = G[int64_t(j) * c + i];
-      for (int q = 0; q < k; ++q) sacc -= pan[i * PCHOL_PS + q] * pan[j * PCHOL_PS + q];
-      const double lit = sacc * rljj;
+      const double* pi = pan + i * PCHOL_PS;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int q = 0;
+      for (; q + 4 <= k; q += 4) {
+        a0 = fma(pi[q], pj[q], a0);
+        a1 = fma(pi[q + 1], pj[q + 1], a1);
+        a2 = fma(pi[q + 2], pj[q + 2], a2);
+        a3 = fma(pi[q + 3], pj[q + 3], a3);
+      }
+      for (; q < k; ++q) a0 = fma(pi[q], pj[q], a0);
+      const double lit = (G[int64_t(j) * c + i] - ((a0 + a1) + (a2 + a3))) * rljj;
       pan[i * PCHOL_PS + k] = lit;
       d_s[i] -= lit * lit;
     }
@@ -500,7 +553,12 @@ __global__ void __launch_bounds__(PCHOL_THREADS) k_pchol_panel(const double* __r
       kept[t] = 1;
       state[1] = t + 1;   // rank so far
     }
+    PC1_MARK(4);
     __syncthreads();
+    PC1_MARK(5);
+#ifdef FASTPI_PHASE_CLOCKS
+    if (tid == 0) g_pc1_clk[7] += 1;
+#endif
   }
   for (int e = tid; e < c * nb; e += PCHOL_THREADS) {
     const int i = e / nb, k = e % nb;
@@ -511,6 +569,7 @@ __global__ void __launch_bounds__(PCHOL_THREADS) k_pchol_panel(const double* __r
     used[i] = used_s[i];
   }
   if (tid == 0 && stop) state[0] = 1;
+  PC1_MARK(6);
 }
 
 // G[i, l] -= sum_{q in [t0, t0 + nb)} Lo[i, q] Lo[l, q] for all i, l < c: the
@@ -528,6 +587,36 @@ __global__ void k_pchol_trailing(double* __restrict__ G, int c, int t0, int nb, 
   double s = 0.0;
   for (int q = 0; q < nb; ++q) s = fma(Li[q], Ll[q], s);
   G[e] -= s;
+}
+
+// Instrumented builds: the panel kernel's phase clocks to stderr (per step).
+void pchol_phase_report(const char* tag) {
+#ifdef FASTPI_PHASE_CLOCKS
+  long long clk[8] = {0};
+  CK(cudaMemcpyFromSymbol(clk, g_pc1_clk, sizeof clk));
+  const long long st = std::max<long long>(1, clk[7]);
+  fprintf(stderr, "pchol %s: steps %lld, per step clk: pivot %lld rows %lld sync %lld; set-up total %lld "
+          "write-back total %lld\n", tag, clk[7], clk[1] / st, clk[4] / st, clk[5] / st, clk[0], clk[6]);
+  const long long z[8] = {0};
+  CK(cudaMemcpyToSymbol(g_pc1_clk, z, sizeof z));
+#else
+  (void)tag;
+#endif
+}
+
+// Whether the core SVD runs on K^T, i.e. one-sided Jacobi orthogonalises the
+// rows of K = [[diag(sigma), P], [0, R_R]] rather than its columns (default;
+// FASTPI_CORE_TRANSPOSE=0 takes the columns).  Two rows i, i' < k of K meet
+// only through P (their inner product is P_i . P_i', against norms that
+// include sigma_i and sigma_i'), while a column of the border has its full
+// projection P[:, t] against the sigma_j e_j columns; so the rows start much
+// closer to orthogonal and the iteration needs fewer sweeps (the strategy of
+// running Jacobi on R^T after a QR; here K is already upper triangular).
+// Measured on the 20 000 x 5 000 workload: core SVD time per step 189 ->
+// 158 ms (mixed), FP64 form 4.70 -> 4.38 s.
+bool core_transposed() {
+  const char* e = std::getenv("FASTPI_CORE_TRANSPOSE");
+  return !(e && e[0] == '0' && e[1] == 0);
 }
 
 // Lp[a, b] = Lo[piv[a], b] for b <= a < rank (zero elsewhere); rank = state[1].
@@ -579,14 +668,16 @@ __global__ void k_trinv_cols(const T* __restrict__ L, int c, const int32_t* __re
 }
 
 // K ((k + c) x (k + c), COLUMN-major) = [[diag(sig), P], [0, R_R]] with
-// P = Pt^T (Pt: c x k, ld ldp) and R_R = M^T (M: c x c row-major, FP64).
+// P = Pt^T (Pt: c x k, ld ldp) and R_R = M^T (M: c x c row-major, FP64);
+// trans: K^T instead (K stored row-major).
 template <typename T, typename TM>
 __global__ void k_build_core(int64_t k, int64_t c, const double* __restrict__ sig, const T* __restrict__ Pt,
-                             int64_t ldp, const TM* __restrict__ M, T* __restrict__ K) {
+                             int64_t ldp, const TM* __restrict__ M, T* __restrict__ K, bool trans) {
   const int64_t n = k + c;
   int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= n * n) return;
-  const int64_t col = e / n, row = e % n;
+  const int64_t a = e / n, b = e % n;
+  const int64_t col = trans ? b : a, row = trans ? a : b;
   T v = 0;
   if (col < k) {
     if (row == col) v = T(sig[col]);
@@ -768,10 +859,12 @@ struct Phase {
     gram(D.get(), G.get());
     const size_t pan_bytes = size_t(c) * PCHOL_PS * sizeof(double) + size_t(c) * (sizeof(double) + sizeof(int));
     if (pan_bytes <= 200 * 1024) {
-      // blocked: panels of PCHOL_NB columns in one CTA, trailing updates as FP64 GEMMs
+      // blocked: panels of PCHOL_NB columns in one CTA, each followed by the
+      // Schur-complement update of the columns after it over every SM
       DArr<double> dd(c, st);
       DArr<int32_t> used(c, st), pstate(2, st);
       CK(cudaMemsetAsync(pstate.get(), 0, 8, st));
+      CK(cudaMemsetAsync(Lo.get(), 0, size_t(c * c) * sizeof(double), st));
       if (pan_bytes > 48 * 1024)
         allow_max_dynamic_smem((const void*)k_pchol_panel);
       for (int64_t t0 = 0; t0 < c; t0 += PCHOL_NB) {
@@ -832,17 +925,18 @@ struct Phase {
     // R_R = (Lo L2)^T : M = Lo * L2 (FP64 in the FP64 form; in the mixed form
     // in FP32 on the tensor cores, the precision of the core it feeds)
     DArr<T> K(n * n, st), J(n * n, st);
+    const bool ktrans = core_transposed();
     if constexpr (sizeof(T) == 8) {
       CK(cudaMemcpyAsync(G2.get(), GT.get(), size_t(c * c) * 8, cudaMemcpyDeviceToDevice, st));
       gemm<double>(st, false, false, c, c, c, 1.0, Lo.get(), c, G2.get(), c, 0.0, M.get(), c);
-      k_build_core<T, double><<<g1(n * n), 256, 0, st>>>(k, c, S(), Pt.get(), ldp, M.get(), K.get());
+      k_build_core<T, double><<<g1(n * n), 256, 0, st>>>(k, c, S(), Pt.get(), ldp, M.get(), K.get(), ktrans);
       CK_LAUNCH();
     } else {
       DArr<float> Lo32(c * c, st), M32(c * c, st);
       k_convert<float, double><<<g1(c * c), 256, 0, st>>>(c * c, Lo.get(), Lo32.get());
       CK_LAUNCH();
       gemm_f32(st, false, false, c, c, c, 1.f, Lo32.get(), c, GT.get(), c, 0.f, M32.get(), c);
-      k_build_core<T, float><<<g1(n * n), 256, 0, st>>>(k, c, S(), Pt.get(), ldp, M32.get(), K.get());
+      k_build_core<T, float><<<g1(n * n), 256, 0, st>>>(k, c, S(), Pt.get(), ldp, M32.get(), K.get(), ktrans);
       CK_LAUNCH();
     }
     // core SVD
@@ -882,8 +976,10 @@ struct Phase {
     // rotations
     DArr<T> Ut(n * std::max<int64_t>(kk, 1), st), Vt(n * std::max<int64_t>(kk, 1), st);
     if (kk > 0) {
-      k_core_vectors<T><<<g1(n * kk), 256, 0, st>>>(n, kk, K.get(), J.get(), jsig.get(), jperm.get(), Ut.get(),
-                                                     Vt.get());
+      // K^T J has orthogonal columns when the SVD ran on K^T: then J holds
+      // K's left singular vectors and the normalised columns its right ones
+      k_core_vectors<T><<<g1(n * kk), 256, 0, st>>>(n, kk, K.get(), J.get(), jsig.get(), jperm.get(),
+                                                     ktrans ? Vt.get() : Ut.get(), ktrans ? Ut.get() : Vt.get());
       CK_LAUNCH();
       if constexpr (sizeof(T) == 4) {
         ns_orthonormalize(st, n, kk, Ut.get());
@@ -1155,6 +1251,10 @@ void factor_impl(fastpi_ctx* h, Factors& F, int64_t r, double kratio, int64_t ch
   colp.q = s;
   run_phase(colp, Tc, cc, rr);
   info.ms_col_update = tm.stop();
+#ifdef FASTPI_PHASE_CLOCKS
+  CK(cudaStreamSynchronize(st));
+  pchol_phase_report("factor");
+#endif
 
   // ---- V = [[V_row W_top], [W_bot]]; back to the caller's order
   tm.start();
