@@ -223,9 +223,9 @@ def oracle_sample(w, chunks, budget_s: float = 60.0):
 # (ncu dram__bytes_read.sum + dram__bytes_write.sum, three row-phase cores of
 # n = 531 and three column-phase cores of n = 756), averaged over the 40 core
 # launches of a step by their counts (32 row-phase, 8 column-phase).
-JACOBI_TRAFFIC_BYTES = (32 * 2.9525333e6 + 8 * 5.8988373e6) / 40
+JACOBI_TRAFFIC_BYTES = (32 * 3.0440000e6 + 8 * 5.9398880e6) / 40
 JACOBI_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_jacobi_cluster<16, 0, 1>: "
-                         "2.95 MB per row-phase core (n = 531), 5.90 MB per column-phase core (n = 756), "
+                         "3.04 MB per row-phase core (n = 531), 5.94 MB per column-phase core (n = 756), "
                          "weighted 32 : 8 as in one step (profiles/k_jacobi_cluster_medium.md)")
 
 
