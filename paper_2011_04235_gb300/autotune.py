@@ -4,7 +4,7 @@ include/fastpi.h, ``fastpi_load_tuning``).
 
   python -m paper_2011_04235_gb300.autotune [--workloads medium,large] [--out PATH] [--quick]
 
-Three searches, each timed with CUDA events on the device:
+Four searches, each timed with CUDA events on the device:
 
 1. Core-SVD tiling (the FP32 block-Jacobi SVD of the update cores of Eqs. 2
    and 3): for core sizes n from 96 to 2 400, every tiling -- panels of 16 or
@@ -23,6 +23,10 @@ Three searches, each timed with CUDA events on the device:
    block stage alone (fastpi_block_svd) with the natural register-tile
    classes and with the small classes merged into larger ones (fewer
    launches, larger tiles); the fastest layout per precision.
+4. The smallest FP32 product sent to the tensor cores in the mixed form
+   (2 M N K flops; below it the SIMT kernel runs it): the mixed factorization
+   of every workload, with the tables of steps 1-3, for thresholds from 2^24
+   to 2^31 flops; the fastest sum wins.
 
 The table is written to --out (default: the package's tuning.txt) and
 printed; the measurements behind it are printed as JSON lines.
@@ -176,12 +180,38 @@ def tune_buckets(names, base_lines, quick: bool):
     return table, log
 
 
+GEMM_THRESHOLDS = [1 << 24, 1 << 26, 1 << 27, 1 << 28, 1 << 29, 1 << 30, 1 << 31]
+
+
+def tune_gemm(names, base_lines, quick: bool):
+    log, best = [], None
+    for thr in ([1 << 24, 1 << 27, 1 << 29] if quick else GEMM_THRESHOLDS):
+        with tempfile.NamedTemporaryFile("w", suffix=".txt", delete=False) as fh:
+            fh.write("\n".join(base_lines + [f"gemm {thr}"]) + "\n")
+            path = fh.name
+        fastpi.load_tuning(path)
+        os.unlink(path)
+        total = 0.0
+        for name in names:
+            w = workloads.make(name, with_y=False)
+            cfg = w["cfg"]
+            h = fastpi.FastPI(w["m"], w["n"], w["rowptr"], w["col"], w["val"], device=DEV)
+            _factor_ms(h, cfg.r, cfg.k, "mixed", 0, 0)                     # warm-up
+            ms = min(_factor_ms(h, cfg.r, cfg.k, "mixed", 0, 0)[0] for _ in range(1 if quick else 2))
+            h.close()
+            total += ms
+            log.append({"search": "gemm", "tc_min_flops": thr, "workload": name, "ms_factor": ms})
+        if best is None or total < best[0]:
+            best = (total, thr)
+    return [f"gemm {best[1]}"], log
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--workloads", default="medium,large")
     ap.add_argument("--out", default=fastpi.TUNING_PATH)
     ap.add_argument("--quick", action="store_true")
-    ap.add_argument("--skip", default="", help="comma list of searches to skip: core,chunk,bucket")
+    ap.add_argument("--skip", default="", help="comma list of searches to skip: core,chunk,bucket,gemm")
     args = ap.parse_args(argv)
     from paper_2011_04235_gb300 import build
     build.build()
@@ -202,8 +232,12 @@ def main(argv=None):
     bucket_lines, log = ([], []) if "bucket" in skip else tune_buckets(names, core_lines + chunk_lines, args.quick)
     for r in log:
         print(json.dumps(r))
+    gemm_lines, log = ([], []) if "gemm" in skip else tune_gemm(names, core_lines + chunk_lines + bucket_lines,
+                                                                 args.quick)
+    for r in log:
+        print(json.dumps(r))
     lines = (["# written by python -m paper_2011_04235_gb300.autotune on " + torch.cuda.get_device_name(DEV)]
-             + core_lines + chunk_lines + bucket_lines)
+             + core_lines + chunk_lines + bucket_lines + gemm_lines)
     with open(args.out, "w") as fh:
         fh.write("\n".join(lines) + "\n")
     fastpi.load_tuning(args.out)

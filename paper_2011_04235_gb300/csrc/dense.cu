@@ -9,7 +9,10 @@
 // not depend on scheduling).
 #include <algorithm>
 
+#include <cstdlib>
+
 #include "dense.cuh"
+#include "tuning.cuh"
 
 namespace fastpi {
 namespace {
@@ -286,10 +289,20 @@ void gemm(cudaStream_t st, bool ta, bool tb, int64_t M, int64_t N, int64_t K, T 
   gemm_mixed<T, T>(st, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
+// Smallest product (2 M N K flops) sent to the tensor cores: the tuning
+// table's value (below it the SIMT kernel's shorter start-up wins; measured
+// on the 20 000 x 5 000 workload's step), else 2^24; FASTPI_TC_MIN_FLOPS
+// overrides both.
+static double tc_min_flops() {
+  const char* e = std::getenv("FASTPI_TC_MIN_FLOPS");
+  const double x = e && *e ? std::atof(e) : 0.0;
+  return x > 0 ? x : tuned_tc_min_flops(double(1 << 24));
+}
+
 void gemm_f32(cudaStream_t st, bool ta, bool tb, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
               int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc) {
   const double work = 2.0 * double(M) * double(N) * double(K);
-  if (M >= 64 && work >= double(1 << 24) && gemm_tf32_supported(ta, tb, M, N, K, lda, ldb, ldc, A, B, C))
+  if (M >= 64 && work >= tc_min_flops() && gemm_tf32_supported(ta, tb, M, N, K, lda, ldb, ldc, A, B, C))
     gemm_tf32(st, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 3);
   else
     gemm<float>(st, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);

@@ -388,7 +388,8 @@ __global__ void k_pchol(const double* G, int c, const double* dn, double tol, do
 // ascending; no FP64 compare), one thread takes the square root and the
 // reciprocal and hands them to the others, and the row update splits its dot
 // product over four independent accumulators, issued before the load of the
-// pivot's row of G that it ends with.
+// pivot's row of G that it ends with.  (Loading every thread's entries of all
+// eight warp winners' rows while the last reduction runs was measured slower.)
 constexpr int PCHOL_NB = 32;
 constexpr int PCHOL_PS = PCHOL_NB + 1;   // panel row stride: odd, so a warp's rows fall in different banks
 constexpr int PCHOL_THREADS = 256;

@@ -155,29 +155,33 @@ __global__ void __launch_bounds__(CT) k_jacobi_cluster(ClArgs a) {
         const int g = tid < B ? bi * B + tid : bj * B + (tid - B);
         s_gcol[tid] = g < n ? g : -1;
       }
-      // 1. wait until the previous round on this part of both blocks is done
-      if (tid == 0) {
+      // 1. wait until the previous round on this part of both blocks is done:
+      // lanes 0 and 1 poll the two counters with one load instruction, so the
+      // two acquire latencies overlap
+      if (tid < 2) {
+        const bool needed = (need & (tid == 0 ? 1 : 2)) != 0;
+        const unsigned* vp = a.ver + (size_t(tid == 0 ? bi : bj) * C + part) * VER_STRIDE;
         int ok = 1;
-        {
-          const unsigned* vi = a.ver + (size_t(bi) * C + part) * VER_STRIDE;
-          const unsigned* vj = a.ver + (size_t(bj) * C + part) * VER_STRIDE;
-          auto ready = [&] {
-            return (!(need & 1) || b_ld_acquire(vi) >= t) && (!(need & 2) || b_ld_acquire(vj) >= t);
-          };
-          if (!ready()) {
-            const unsigned long long t0 = b_gtimer();
-            unsigned spins = 0;
-            while (!ready()) {
-              if ((++spins & 63u) == 0 && b_gtimer() - t0 > B_WAIT_NS) {
-                atomicOr(a.status, ST_BARRIER_TIMEOUT);
-                ok = 0;
-                break;
-              }
+        bool rdy = !needed || b_ld_acquire(vp) >= t;
+        if (!__all_sync(0x3u, rdy)) {
+          const unsigned long long t0 = b_gtimer();
+          unsigned spins = 0;
+          for (;;) {
+            if (!rdy) rdy = b_ld_acquire(vp) >= t;
+            if (__all_sync(0x3u, rdy)) break;
+            int late = 0;
+            if ((++spins & 63u) == 0) late = (b_gtimer() - t0 > B_WAIT_NS) ? 1 : 0;
+            if (__shfl_sync(0x3u, late, 0)) {   // lane 0 decides for both
+              if (tid == 0) atomicOr(a.status, ST_BARRIER_TIMEOUT);
+              ok = 0;
+              break;
             }
           }
         }
-        s_ok = ok;
-        s_pair_rot = 0;
+        if (tid == 0) {
+          s_ok = ok;
+          s_pair_rot = 0;
+        }
       }
       __syncthreads();
       const bool ok = s_ok != 0;
@@ -366,11 +370,9 @@ __global__ void __launch_bounds__(CT) k_jacobi_cluster(ClArgs a) {
       }
       __syncthreads();
       CPHASE_MARK(4);
-      // hand this part of both blocks to the next round
-      if (tid == 0) {
-        b_st_release(a.ver + (size_t(bi) * C + part) * VER_STRIDE, t + 1u);
-        b_st_release(a.ver + (size_t(bj) * C + part) * VER_STRIDE, t + 1u);
-      }
+      // hand this part of both blocks to the next round (lanes 0 and 1: one
+      // release instruction for the two counters)
+      if (tid < 2) b_st_release(a.ver + (size_t(tid == 0 ? bi : bj) * C + part) * VER_STRIDE, t + 1u);
       if (rr == a.nb - 2) {
         // end of a sweep: combine the rotation flags of all CTAs (the flags
         // of the CTAs of one cluster are equal)

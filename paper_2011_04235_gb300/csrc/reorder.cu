@@ -121,6 +121,118 @@ __global__ void k_flags_active(const uint8_t* act, const int32_t* label, int32_t
   flags[i] = f;
 }
 
+// One CTA for a small compaction (cnt <= CS_MAX): the flags of
+// k_flags_active (roots = 1: those of k_flags_roots instead), a block-wide
+// prefix sum and the scatter of k_compact, in one launch.  Thread t owns the
+// consecutive indices [t E, (t + 1) E), so the output keeps the ascending
+// order of i, as the three-launch form does.
+constexpr int CS_THREADS = 1024;
+constexpr int CS_PER = 32;
+constexpr int64_t CS_MAX = int64_t(CS_THREADS) * CS_PER;
+__global__ void __launch_bounds__(CS_THREADS) k_compact_small(const uint8_t* act, const int32_t* label, int32_t gcc,
+                                                              int roots, int64_t base, int64_t cnt,
+                                                              const int32_t* keysrc, int32_t key_bias, int key_neg,
+                                                              uint32_t* out_ids, uint32_t* out_keys) {
+  __shared__ int wsum[CS_THREADS / 32];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int E = int((cnt + CS_THREADS - 1) / CS_THREADS);
+  const int64_t i0 = int64_t(tid) * E;
+  unsigned bits = 0;   // E <= 32
+  for (int e = 0; e < E; ++e) {
+    const int64_t i = i0 + e;
+    if (i >= cnt) break;
+    const int64_t v = base + i;
+    int f;
+    if (roots)
+      f = act[v] && label[v] == int32_t(v) && int32_t(v) != gcc;
+    else {
+      f = act[v] != 0;
+      if (label && f) f = label[v] != gcc;
+    }
+    bits |= unsigned(f) << e;
+  }
+  const int own = __popc(bits);
+  int inc = own;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const int x = wsum[lane];
+    int xi = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += t;
+    }
+    wsum[lane] = xi - x;
+  }
+  __syncthreads();
+  int p = wsum[w] + inc - own;
+  for (int e = 0; e < E; ++e) {
+    if (!((bits >> e) & 1u)) continue;
+    const int64_t i = i0 + e;
+    out_ids[p] = uint32_t(i);
+    if (out_keys) {
+      const int32_t kv = keysrc[base + i];
+      out_keys[p] = uint32_t(key_neg ? key_bias - kv : kv);
+    }
+    ++p;
+  }
+}
+
+// One CTA: sorts n <= SS_MAX (key, id) pairs by key, then id, with a bitonic
+// network on the 64-bit words (key << 32 | id) in shared memory.  Where the
+// ids arrive in ascending order (every caller here: they come from an
+// ascending compaction) and are distinct, this is exactly the stable sort by
+// key that radix_sort_pairs computes.
+constexpr int SS_THREADS = 1024;
+constexpr int64_t SS_MAX = 16384;
+__global__ void __launch_bounds__(SS_THREADS) k_sort_small(uint32_t* keys, uint32_t* ids, int n, int np2) {
+  extern __shared__ unsigned long long sk[];
+  for (int i = threadIdx.x; i < np2; i += SS_THREADS)
+    sk[i] = i < n ? ((static_cast<unsigned long long>(keys[i]) << 32) | ids[i]) : ~0ull;
+  __syncthreads();
+  for (int size = 2; size <= np2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < np2 / 2; t += SS_THREADS) {
+        const int lo = 2 * t - (t & (stride - 1));   // index with bit `stride` clear
+        const int hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const unsigned long long a = sk[lo], b = sk[hi];
+        if ((a > b) == up) {
+          sk[lo] = b;
+          sk[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += SS_THREADS) {
+    keys[i] = uint32_t(sk[i] >> 32);
+    ids[i] = uint32_t(sk[i]);
+  }
+}
+
+// Sorts the (key, id) pairs of the reordering (ids ascending and distinct on
+// entry): one CTA when they fit, else the multi-pass radix sort.
+void sort_key_id(uint32_t* keys, uint32_t* ids, int64_t n, int bits, cudaStream_t st) {
+  if (n <= 1) return;
+  if (n <= SS_MAX) {
+    int np2 = 2;
+    while (np2 < n) np2 <<= 1;
+    const size_t smem = size_t(np2) * 8;
+    if (smem > 48 * 1024) allow_max_dynamic_smem((const void*)k_sort_small);
+    k_sort_small<<<1, SS_THREADS, smem, st>>>(keys, ids, int(n), np2);
+    CK_LAUNCH();
+    return;
+  }
+  radix_sort_pairs(keys, ids, n, bits, st);
+}
+
 // roots of non-giant components: active v with label[v] == v and v != gcc
 __global__ void k_flags_roots(const uint8_t* act, const int32_t* label, int32_t gcc, int64_t cnt, int32_t* flags) {
   int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -156,11 +268,6 @@ __global__ void k_place_hubs(const uint32_t* sorted_ids, int64_t count, int64_t 
 __global__ void k_place_front(const uint32_t* sorted_ids, int64_t count, int64_t front, int32_t* order) {
   int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t < count) order[front + t] = int32_t(sorted_ids[t]);
-}
-
-__global__ void k_cc_init(int32_t* parent, int64_t N) {
-  int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (v < N) parent[v] = int32_t(v);
 }
 
 __device__ __forceinline__ int32_t uf_find(int32_t* parent, int32_t x) {
@@ -270,13 +377,50 @@ __global__ void k_inverse_perm(const int32_t* order, int64_t n, int32_t* pos) {
   if (t < n) pos[order[t]] = int32_t(t);
 }
 
-// Compact the ids i in [0, cnt) whose node (base + i) passes the predicate;
-// optionally with keys.  Returns the count (synchronous).
-struct Compactor {
-  cudaStream_t st;
-  DArr<int32_t> flags, pos, count;
-  Compactor(int64_t cap, cudaStream_t s) : st(s), flags(cap, s), pos(cap, s), count(1, s) {}
+// A second stream and two events for the parts of an iteration in which the
+// rows and the columns are handled independently (fork: the side stream waits
+// for the main one; join: the main one waits for the side one).  Destroyed
+// with the object; a stream destroyed with work pending finishes that work.
+struct SideStream {
+  cudaStream_t st = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  SideStream() {
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+  }
+  ~SideStream() {
+    if (join) cudaEventDestroy(join);
+    if (fork) cudaEventDestroy(fork);
+    if (st) cudaStreamDestroy(st);
+  }
+  SideStream(const SideStream&) = delete;
+  SideStream& operator=(const SideStream&) = delete;
+  void start(cudaStream_t main) {
+    CK(cudaEventRecord(fork, main));
+    CK(cudaStreamWaitEvent(st, fork, 0));
+  }
+  void finish(cudaStream_t main) {
+    CK(cudaEventRecord(join, st));
+    CK(cudaStreamWaitEvent(main, join, 0));
+  }
 };
+
+// Per-iteration reset of the component state: parent[v] = v and zero counts,
+// the GCC key and the root count.
+__global__ void k_cc_reset(int32_t* parent, int32_t* cntT, int32_t* cntF, int64_t N, unsigned long long* best,
+                           int32_t* nroots) {
+  int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (v == 0) {
+    *best = 0ull;
+    *nroots = 0;
+  }
+  if (v < N) {
+    parent[v] = int32_t(v);
+    cntT[v] = 0;
+    cntF[v] = 0;
+  }
+}
 
 }  // namespace
 
@@ -341,8 +485,13 @@ void run_reorder(fastpi_ctx* h, double k, Reordering& R) {
     CK_LAUNCH();
   }
   const int64_t cap = N + 1;
+  // scratch of the main stream (rows, components) and of the side stream (columns)
   DArr<int32_t> flags(cap, st), pos(cap, st), dcount(4, st);
   DArr<uint32_t> ids(cap, st), keys(cap, st);
+  DArr<int32_t> flags2(cap, st), pos2(cap, st), dcount2(4, st);
+  DArr<uint32_t> ids2(cap, st), keys2(cap, st);
+  SideStream side;
+  cudaStream_t st2 = side.st;
   DArr<int64_t> bT(cap, st), bF(cap, st), d_row_off(cap + 1, st), d_col_off(cap + 1, st), summ(4, st);
   DArr<unsigned long long> best(1, st);
   DArr<int32_t> dnroots(1, st);
@@ -352,14 +501,26 @@ void run_reorder(fastpi_ctx* h, double k, Reordering& R) {
   // compact the active nodes of one side (plus keys); `known` is the number
   // of nodes that pass, which the host always knows from the counts of the
   // iteration (active instances / features, the GCC's size), so no read-back
-  auto compact = [&](int64_t base, int64_t cnt, const int32_t* lab, int32_t gcc, const int32_t* keysrc,
+  // side 0: rows on the main stream, side 1: columns on the side stream
+  auto compact = [&](int sd, int64_t base, int64_t cnt, const int32_t* lab, int32_t gcc, const int32_t* keysrc,
                      int32_t key_bias, int key_neg, int64_t known) -> int64_t {
     if (cnt == 0 || known == 0) return 0;
-    k_flags_active<<<nblk(cnt), BS, 0, st>>>(act, lab, gcc, base, cnt, flags);
+    cudaStream_t cs = sd ? st2 : st;
+    if (cnt <= CS_MAX) {
+      k_compact_small<<<1, CS_THREADS, 0, cs>>>(act, lab, gcc, 0, base, cnt, keysrc, key_bias, key_neg,
+                                                sd ? ids2.get() : ids.get(),
+                                                keysrc ? (sd ? keys2.get() : keys.get()) : nullptr);
+      CK_LAUNCH();
+      return known;
+    }
+    int32_t* fl = sd ? flags2.get() : flags.get();
+    int32_t* ps = sd ? pos2.get() : pos.get();
+    k_flags_active<<<nblk(cnt), BS, 0, cs>>>(act, lab, gcc, base, cnt, fl);
     CK_LAUNCH();
-    exclusive_scan_i32(flags, pos, cnt, st);
-    k_compact<<<nblk(cnt), BS, 0, st>>>(flags, pos, cnt, keysrc, base, key_bias, key_neg, ids,
-                                        keysrc ? keys.get() : nullptr, dcount);
+    exclusive_scan_i32(fl, ps, cnt, cs);
+    k_compact<<<nblk(cnt), BS, 0, cs>>>(fl, ps, cnt, keysrc, base, key_bias, key_neg, sd ? ids2.get() : ids.get(),
+                                        keysrc ? (sd ? keys2.get() : keys.get()) : nullptr,
+                                        sd ? dcount2.get() : dcount.get());
     CK_LAUNCH();
     return known;
   };
@@ -375,28 +536,28 @@ void run_reorder(fastpi_ctx* h, double k, Reordering& R) {
     CK_LAUNCH();
     k_deg_cols<<<nblk(n * 32), BS, 0, st>>>(h->colptr, h->csc_row, act, m, n, deg);
     CK_LAUNCH();
-    // hubs: instances (key = n - deg so that ascending key = degree descending)
+    // hubs (key = n - deg so that ascending key = degree descending): the
+    // rows here, the columns on the side stream (each side reads and clears
+    // only its own part of act and deg)
+    side.start(st);
     if (m_hub > 0) {
-      int64_t c = compact(0, m, nullptr, 0, deg, int32_t(n), 1, nI);
-      radix_sort_pairs(keys, ids, c, bits_for(uint64_t(n)), st);
+      int64_t c = compact(0, 0, m, nullptr, 0, deg, int32_t(n), 1, nI);
+      sort_key_id(keys, ids, c, bits_for(uint64_t(n)), st);
       k_place_hubs<<<nblk(m_hub), BS, 0, st>>>(ids, m_hub, bTc, 0, R.row_order, act);
       CK_LAUNCH();
       bTc -= m_hub;
     }
     if (n_hub > 0) {
-      int64_t c = compact(m, n, nullptr, 0, deg, int32_t(m), 1, nF);
-      radix_sort_pairs(keys, ids, c, bits_for(uint64_t(m)), st);
-      k_place_hubs<<<nblk(n_hub), BS, 0, st>>>(ids, n_hub, bFc, m, R.col_order, act);
+      int64_t c = compact(1, m, n, nullptr, 0, deg, int32_t(m), 1, nF);
+      sort_key_id(keys2, ids2, c, bits_for(uint64_t(m)), st2);
+      k_place_hubs<<<nblk(n_hub), BS, 0, st2>>>(ids2, n_hub, bFc, m, R.col_order, act);
       CK_LAUNCH();
       bFc -= n_hub;
     }
-    // connected components of G'
-    k_cc_init<<<nblk(N), BS, 0, st>>>(parent, N);
+    // connected components of G' (the reset overlaps the columns' hubs)
+    k_cc_reset<<<nblk(N), BS, 0, st>>>(parent, cntT, cntF, N, best, dnroots);
     CK_LAUNCH();
-    CK(cudaMemsetAsync(cntT.get(), 0, size_t(N) * 4, st));
-    CK(cudaMemsetAsync(cntF.get(), 0, size_t(N) * 4, st));
-    CK(cudaMemsetAsync(best.get(), 0, 8, st));
-    CK(cudaMemsetAsync(dnroots.get(), 0, 4, st));
+    side.finish(st);
     if (nnz > 0) {
       k_cc_hook<<<nblk(nnz), BS, 0, st>>>(nz_row, h->col, act, m, nnz, parent, h->dstatus);
       CK_LAUNCH();
@@ -417,26 +578,33 @@ void run_reorder(fastpi_ctx* h, double k, Reordering& R) {
     // non-giant components: front positions in (label asc, id asc)
     // rows of the non-giant components: the active rows less the hubs just
     // placed and the GCC's rows (likewise for the features)
-    int64_t cT = compact(0, m, label, gcc, label, 0, 0, nI - m_hub - sm[1]);
+    // (the columns on the side stream again)
+    side.start(st);
+    int64_t cT = compact(0, 0, m, label, gcc, label, 0, 0, nI - m_hub - sm[1]);
     if (cT > 0) {
-      radix_sort_pairs(keys, ids, cT, bits_for(uint64_t(N)), st);
+      sort_key_id(keys, ids, cT, bits_for(uint64_t(N)), st);
       k_place_front<<<nblk(cT), BS, 0, st>>>(ids, cT, fT, R.row_order);
       CK_LAUNCH();
     }
-    int64_t cF = compact(m, n, label, gcc, label, 0, 0, nF - n_hub - sm[2]);
+    int64_t cF = compact(1, m, n, label, gcc, label, 0, 0, nF - n_hub - sm[2]);
     if (cF > 0) {
-      radix_sort_pairs(keys, ids, cF, bits_for(uint64_t(N)), st);
-      k_place_front<<<nblk(cF), BS, 0, st>>>(ids, cF, fF, R.col_order);
+      sort_key_id(keys2, ids2, cF, bits_for(uint64_t(N)), st2);
+      k_place_front<<<nblk(cF), BS, 0, st2>>>(ids2, cF, fF, R.col_order);
       CK_LAUNCH();
     }
     // one block per non-giant component, in ascending label (= root id) order
     const int64_t nroots = sm[3];
     if (nroots > 0) {
-      k_flags_roots<<<nblk(N), BS, 0, st>>>(act, label, gcc, N, flags);
-      CK_LAUNCH();
-      exclusive_scan_i32(flags, pos, N, st);
-      k_compact<<<nblk(N), BS, 0, st>>>(flags, pos, N, nullptr, 0, 0, 0, ids, nullptr, dcount);
-      CK_LAUNCH();
+      if (N <= CS_MAX) {
+        k_compact_small<<<1, CS_THREADS, 0, st>>>(act, label, gcc, 1, 0, N, nullptr, 0, 0, ids, nullptr);
+        CK_LAUNCH();
+      } else {
+        k_flags_roots<<<nblk(N), BS, 0, st>>>(act, label, gcc, N, flags);
+        CK_LAUNCH();
+        exclusive_scan_i32(flags, pos, N, st);
+        k_compact<<<nblk(N), BS, 0, st>>>(flags, pos, N, nullptr, 0, 0, 0, ids, nullptr, dcount);
+        CK_LAUNCH();
+      }
       k_block_counts<<<nblk(nroots), BS, 0, st>>>(ids, nroots, cntT, cntF, bT, bF);
       CK_LAUNCH();
       exclusive_scan_i64(bT, bT, nroots, st);
@@ -448,6 +616,7 @@ void run_reorder(fastpi_ctx* h, double k, Reordering& R) {
     nb += nroots;
     fT += cT;
     fF += cF;
+    side.finish(st);
     // recurse on the GCC
     k_keep_gcc<<<nblk(N), BS, 0, st>>>(act, label, gcc, N);
     CK_LAUNCH();
@@ -457,13 +626,13 @@ void run_reorder(fastpi_ctx* h, double k, Reordering& R) {
   }
   // the final GCC fills the middle positions and forms the last A11 block
   if (nI + nF > 0) {
-    int64_t c = compact(0, m, nullptr, 0, nullptr, 0, 0, nI);
+    int64_t c = compact(0, 0, m, nullptr, 0, nullptr, 0, 0, nI);
     if (c > 0) {
       k_place_front<<<nblk(c), BS, 0, st>>>(ids, c, fT, R.row_order);
       CK_LAUNCH();
     }
     fT += c;
-    int64_t c2 = compact(m, n, nullptr, 0, nullptr, 0, 0, nF);
+    int64_t c2 = compact(0, m, n, nullptr, 0, nullptr, 0, 0, nF);
     if (c2 > 0) {
       k_place_front<<<nblk(c2), BS, 0, st>>>(ids, c2, fF, R.col_order);
       CK_LAUNCH();

@@ -15,6 +15,9 @@
 //         batched Jacobi of the A11 blocks: problems whose longer side is
 //         <= dim_max run in the register-tile class `class` (never below the
 //         class their size needs)
+//   gemm <tc_min_flops>
+//         the mixed form's FP32 products of at least this many flops
+//         (2 M N K) run on the tensor cores, smaller ones on the SIMT kernel
 // The file is read on first use from $FASTPI_TUNING, else from tuning.txt next
 // to libfastpi.so; without one the built-in defaults apply (chunk 256, core
 // tiling by the SM count, natural bucket classes).
@@ -52,6 +55,7 @@ struct Table {
   std::vector<CoreRow> core;
   std::vector<ChunkRow> chunk;
   std::vector<BucketRow> bucket;
+  double tc_min_flops = 0;   // 0: not in the table
 };
 
 std::mutex g_mu;
@@ -98,6 +102,10 @@ bool parse(const std::string& path, Table& t, std::string* why) {
       ok = bool(ss >> r.prec >> r.phase >> r.k_max >> r.c) && (r.prec == 0 || r.prec == 1) &&
            (r.phase == 0 || r.phase == 1) && r.c >= 1;
       if (ok) out.chunk.push_back(r);
+    } else if (kind == "gemm") {
+      double v = 0;
+      ok = bool(ss >> v) && v >= 1.0;
+      if (ok) out.tc_min_flops = v;
     } else if (kind == "bucket") {
       BucketRow r;
       ok = bool(ss >> r.prec >> r.dim_max >> r.cls) && (r.prec == 0 || r.prec == 1) && r.cls >= 0 && r.cls <= 4;
@@ -166,6 +174,11 @@ bool load_tuning(const char* path, std::string* why) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_tab = std::move(t);
   return true;
+}
+
+double tuned_tc_min_flops(double fallback) {
+  const Table& t = table();
+  return t.tc_min_flops > 0 ? t.tc_min_flops : fallback;
 }
 
 std::string tuning_source() { return table().source; }

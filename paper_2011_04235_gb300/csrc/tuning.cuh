@@ -17,6 +17,9 @@ int64_t tuned_chunk(int prec, int phase, int64_t k_target, int64_t fallback);
 // Register-tile class of a batched Jacobi problem whose longer side is dim
 // (never below `natural`, the class its size needs).
 int tuned_bucket_class(int prec, int dim, int natural);
+// Smallest FP32 product (2 M N K flops) of the mixed form sent to the tensor
+// cores; `fallback` when the table has none.
+double tuned_tc_min_flops(double fallback);
 // Replaces the table with the file at path (NULL: the built-in defaults);
 // false, with the reason in *why, when the file cannot be read or parsed.
 bool load_tuning(const char* path, std::string* why);

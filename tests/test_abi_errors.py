@@ -99,9 +99,9 @@ def test_tuning_table_parsing(lib, tmp_path):
     FASTPI_ERR_ARG and a message, and NULL restores the built-in defaults."""
     good = tmp_path / "t.txt"
     good.write_text("# comment\ncore 600 16 4 0 1\ncore 1048576 32 8 1 1\nchunk 1 0 491 320\n"
-                    "chunk 0 1 1099511627776 256\nbucket 1 256 1\n")
+                    "chunk 0 1 1099511627776 256\nbucket 1 256 1\ngemm 536870912\n")
     assert lib.fastpi_load_tuning(str(good).encode()) == 0
-    for bad in ("core 600 24 4 0 1\n", "chunk 2 0 10 256\n", "bucket 1 256 9\n", "core 600 16\n", "foo 1\n"):
+    for bad in ("core 600 24 4 0 1\n", "chunk 2 0 10 256\n", "bucket 1 256 9\n", "core 600 16\n", "foo 1\n", "gemm 0\n", "gemm\n"):
         p = tmp_path / "bad.txt"
         p.write_text(bad)
         assert lib.fastpi_load_tuning(str(p).encode()) == ERR_ARG
