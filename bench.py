@@ -216,17 +216,12 @@ def oracle_sample(w, chunks, budget_s: float = 60.0):
 
 
 # ----------------------------------------------------------------------------- main
-# DRAM bytes (read + write) per launch of the dominant kernel, from an ncu
-# capture of the current kernel on this workload; None whenever the kernel's
-# source changed after the capture, until it is captured again.
-# DRAM read + write per launch of k_jacobi_cluster<16, 0, 1> on this workload
-# (ncu dram__bytes_read.sum + dram__bytes_write.sum, three row-phase cores of
-# n = 531 and three column-phase cores of n = 756), averaged over the 40 core
-# launches of a step by their counts (32 row-phase, 8 column-phase).
-JACOBI_TRAFFIC_BYTES = (32 * 3.0440000e6 + 8 * 5.9398880e6) / 40
-JACOBI_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_jacobi_cluster<16, 0, 1>: "
-                         "3.04 MB per row-phase core (n = 531), 5.94 MB per column-phase core (n = 756), "
-                         "weighted 32 : 8 as in one step (profiles/k_jacobi_cluster_medium.md)")
+# DRAM bytes (read + write) per launch of the dominant kernel,
+# k_jacobi_cluster<16, 0, 1>, from an ncu capture of the current kernel on
+# this workload (dram__bytes_read.sum + dram__bytes_write.sum); None whenever
+# the kernel's source changed after the capture, until it is captured again.
+JACOBI_TRAFFIC_BYTES = None
+JACOBI_TRAFFIC_SOURCE = "null: the kernel changed after the last ncu capture"
 
 
 def pinv_threshold_report(S, m, n):
