@@ -119,4 +119,16 @@ void d2h_sync(void* dst, const void* src, size_t bytes, cudaStream_t st);
 
 int ceil_div_i(int64_t a, int64_t b);
 
+// An unsigned image of a double whose order is the order of the values
+// (non-NaN): the sign bit flipped for non-negative values, all bits flipped
+// for negative ones.  Comparing these on the integer pipe replaces FP64
+// compares, which GB300 runs on its narrow FP64 pipe.
+__device__ __forceinline__ unsigned long long order_key(double v) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double order_value(unsigned long long k) {
+  return __longlong_as_double(static_cast<long long>((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
 }  // namespace fastpi

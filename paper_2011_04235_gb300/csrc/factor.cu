@@ -151,6 +151,50 @@ __global__ void k_spmm_t(const int64_t* __restrict__ ptr, const int32_t* __restr
   }
 }
 
+// The same product with a column's nonzeros split over the CTA's 8 warps (a
+// hub row or column has hundreds of them, and one thread walking them all is
+// a chain of dependent gathers): warp w sums the nonzeros of its contiguous
+// share, lane l the entries j = l + 32 u, u < SP_U (k <= 32 SP_U), and the 8
+// partial sums are added in warp order through shared memory.
+constexpr int SP_WARPS = 8, SP_U = 32;
+template <typename T>
+__global__ void __launch_bounds__(SP_WARPS * 32) k_spmm_t_split(const int64_t* __restrict__ ptr,
+                                                                const int32_t* __restrict__ idx,
+                                                                const double* __restrict__ val, int64_t a, int k,
+                                                                const T* __restrict__ Uc, int64_t ldu,
+                                                                T* __restrict__ Pt, int64_t ldp) {
+  extern __shared__ unsigned char sp_raw[];
+  T* part = reinterpret_cast<T*>(sp_raw);   // [SP_WARPS][k]
+  const int64_t t = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t e0 = ptr[a + t], e1 = ptr[a + t + 1];
+  const int64_t per = (e1 - e0 + SP_WARPS - 1) / SP_WARPS;
+  const int64_t b0 = min(e1, e0 + w * per), b1 = min(e1, b0 + per);
+  T acc[SP_U];
+#pragma unroll
+  for (int u = 0; u < SP_U; ++u) acc[u] = T(0);
+  for (int64_t e = b0; e < b1; ++e) {
+    const T v = T(val[e]);
+    const T* row = Uc + int64_t(idx[e]) * ldu;
+#pragma unroll
+    for (int u = 0; u < SP_U; ++u) {
+      const int j = lane + 32 * u;
+      if (j < k) acc[u] = fma(v, row[j], acc[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < SP_U; ++u) {
+    const int j = lane + 32 * u;
+    if (j < k) part[w * k + j] = acc[u];
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += SP_WARPS * 32) {
+    T s = part[j];
+    for (int q = 1; q < SP_WARPS; ++q) s += part[q * k + j];
+    Pt[t * ldp + j] = s;
+  }
+}
+
 template <typename T>
 __global__ void k_axpy2d(int64_t rows, int64_t cols, const T* X, int64_t ldx, T* Y, int64_t ldy) {
   int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -370,8 +414,6 @@ __global__ void k_pchol(const double* G, int c, const double* dn, double tol, do
   if (threadIdx.x == 0) *rank_out = rank;
 }
 
-// Linv_orig[a, piv[b]] = X[a, b] for a, b < rank (zero elsewhere): the map
-// that turns R (p x c) into Q1 = R Linv_orig^T.
 // Blocked form of k_pchol.  G (c x c, FP64, full symmetric) holds the Schur
 // complement of the columns factored so far (earlier panels are removed from
 // it by k_pchol_trailing after each panel); d / used / Lo / piv / kept / rank
@@ -411,17 +453,6 @@ __device__ long long g_pc1_clk[8];
   do {              \
   } while (0)
 #endif
-
-// An unsigned image of a double whose order is the order of the values
-// (non-NaN): the sign bit flipped for non-negative values, all bits flipped
-// for negative ones.
-__device__ __forceinline__ unsigned long long order_key(double v) {
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
-  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
-__device__ __forceinline__ double order_value(unsigned long long k) {
-  return __longlong_as_double(static_cast<long long>((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
-}
 
 // Within a warp: the largest key, ties to the lowest index (idx = UINT_MAX
 // for lanes without a candidate); every lane gets the result.
@@ -605,6 +636,14 @@ void pchol_phase_report(const char* tag) {
 #endif
 }
 
+// Whether the mixed form factors the residual Gram with diagonal pivoting
+// (default; the FP64 form always does, as the oracle's QR with column
+// pivoting) or with the unpivoted blocked Cholesky (FASTPI_MIXED_PIVOT=0).
+bool mixed_pivoted_cholesky() {
+  const char* e = std::getenv("FASTPI_MIXED_PIVOT");
+  return !(e && e[0] == '0' && e[1] == 0);
+}
+
 // Whether the core SVD runs on K^T, i.e. one-sided Jacobi orthogonalises the
 // rows of K = [[diag(sigma), P], [0, R_R]] rather than its columns (default;
 // FASTPI_CORE_TRANSPOSE=0 takes the columns).  Two rows i, i' < k of K meet
@@ -632,16 +671,16 @@ __global__ void k_gather_lp(const double* Lo, const int32_t* piv, const int32_t*
   if (blockIdx.x == 0 && threadIdx.x == 0) *rank_out = rank;
 }
 
-// One CTA.
+// Lio[a, piv[b]] = X[a, b] for a, b < rank: the inverse of the kept triangle
+// in the original column order, the map that turns R (p x c) into
+// Q1 = R Lio^T; one thread per entry (the caller clears Lio first).
 template <typename E>
 __global__ void k_scatter_inv(const E* X, const int32_t* piv, const int32_t* rank_p, int c, E* Lio) {
   const int rank = *rank_p;
-  for (int64_t e = threadIdx.x; e < int64_t(c) * c; e += blockDim.x) Lio[e] = E(0);
-  __syncthreads();
-  for (int64_t e = threadIdx.x; e < int64_t(rank) * rank; e += blockDim.x) {
-    const int a = int(e / rank), b = int(e % rank);
-    Lio[int64_t(a) * c + piv[b]] = X[int64_t(a) * c + b];
-  }
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= int64_t(rank) * rank) return;
+  const int a = int(e / rank), b = int(e % rank);
+  Lio[int64_t(a) * c + piv[b]] = X[int64_t(a) * c + b];
 }
 
 // X = inverse of L restricted to the kept indices (zero rows / columns for
@@ -812,7 +851,14 @@ struct Phase {
     CK_LAUNCH();
     const int64_t ldp = std::max<int64_t>(k, 1);
     if (k > 0) {
-      k_spmm_t<T><<<unsigned(c), 256, 0, st>>>(sc.ptr, sc.idx, sc.val, a, k, Ucur, kmax, Pt.get(), ldp);
+      if (k <= 32 * SP_U) {
+        const size_t sm = size_t(SP_WARPS) * k * sizeof(T);
+        if (sm > 48 * 1024) allow_max_dynamic_smem((const void*)k_spmm_t_split<T>);
+        k_spmm_t_split<T><<<unsigned(c), SP_WARPS * 32, sm, st>>>(sc.ptr, sc.idx, sc.val, a, int(k), Ucur, kmax,
+                                                                   Pt.get(), ldp);
+      } else {
+        k_spmm_t<T><<<unsigned(c), 256, 0, st>>>(sc.ptr, sc.idx, sc.val, a, k, Ucur, kmax, Pt.get(), ldp);
+      }
       CK_LAUNCH();
       // R = D - Uc P ; second projection pass
       gemm_t<T>(st, false, true, p, c, k, T(-1), Ucur, kmax, Pt.get(), ldp, T(1), D.get(), c);
@@ -859,7 +905,16 @@ struct Phase {
     };
     gram(D.get(), G.get());
     const size_t pan_bytes = size_t(c) * PCHOL_PS * sizeof(double) + size_t(c) * (sizeof(double) + sizeof(int));
-    if (pan_bytes <= 200 * 1024) {
+    if (sizeof(T) == 4 && !mixed_pivoted_cholesky() && c <= 4096) {
+      // mixed form: the blocked FP64 Cholesky without pivoting, spread over
+      // the GPU (the drop rule is the same; the kept directions are taken in
+      // column order instead of by decreasing remaining norm)
+      DArr<int32_t> pstate(2, st);
+      CK(cudaMemsetAsync(pstate.get(), 0, 8, st));
+      chol64_drop_unpivoted(st, G.get(), int(c), dn.get(), drop_tol, Lo.get(), piv.get(), kept.get(), pstate.get());
+      k_gather_lp<<<g1(c * c), 256, 0, st>>>(Lo.get(), piv.get(), pstate.get(), int(c), Lp.get(), rk.get());
+      CK_LAUNCH();
+    } else if (pan_bytes <= 200 * 1024) {
       // blocked: panels of PCHOL_NB columns in one CTA, each followed by the
       // Schur-complement update of the columns after it over every SM
       DArr<double> dd(c, st);
@@ -887,7 +942,8 @@ struct Phase {
     }
     if constexpr (sizeof(T) == 8) {
       trinv(Lp.get(), kept.get(), X.get());
-      k_scatter_inv<double><<<1, 1024, 0, st>>>(X.get(), piv.get(), rk.get(), int(c), Linv.get());
+      CK(cudaMemsetAsync(Linv.get(), 0, size_t(c * c) * sizeof(double), st));
+      k_scatter_inv<double><<<g1(c * c), 256, 0, st>>>(X.get(), piv.get(), rk.get(), int(c), Linv.get());
       CK_LAUNCH();
       to_T(Linv.get(), LinvT.get());
     } else {
@@ -898,7 +954,8 @@ struct Phase {
       k_convert<float, double><<<g1(c * c), 256, 0, st>>>(c * c, Lp.get(), Lp32.get());
       CK_LAUNCH();
       trinv(Lp32.get(), kept.get(), X32.get());
-      k_scatter_inv<float><<<1, 1024, 0, st>>>(X32.get(), piv.get(), rk.get(), int(c), LinvT.get());
+      CK(cudaMemsetAsync(LinvT.get(), 0, size_t(c * c) * sizeof(float), st));
+      k_scatter_inv<float><<<g1(c * c), 256, 0, st>>>(X32.get(), piv.get(), rk.get(), int(c), LinvT.get());
       CK_LAUNCH();
     }
     gemm_t<T>(st, false, true, p, c, c, T(1), D.get(), c, LinvT.get(), c, T(0), Q1.get(), c);
@@ -1255,6 +1312,7 @@ void factor_impl(fastpi_ctx* h, Factors& F, int64_t r, double kratio, int64_t ch
 #ifdef FASTPI_PHASE_CLOCKS
   CK(cudaStreamSynchronize(st));
   pchol_phase_report("factor");
+  chol_drop_phase_report("factor");
 #endif
 
   // ---- V = [[V_row W_top], [W_bot]]; back to the caller's order

@@ -321,13 +321,15 @@ __global__ void k_finish(const DevProb<T>* probs, const int64_t* sig_off, double
   const DevProb<T> pr = probs[blockIdx.x];
   int nq = 1;
   while (nq < pr.q) nq <<= 1;
-  double* key = reinterpret_cast<double*>(smem_raw);
+  // the norms as order-preserving integers: the sort compares on the
+  // integer pipe
+  unsigned long long* key = reinterpret_cast<unsigned long long*>(smem_raw);
   int* idx = reinterpret_cast<int*>(key + nq_max);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   if (norms) {
     // column norms computed beforehand (a single large problem: k_colnorms)
     for (int j = threadIdx.x; j < nq; j += blockDim.x) {
-      key[j] = j < pr.q ? norms[j] : -1.0;
+      key[j] = order_key(j < pr.q ? norms[j] : -1.0);
       idx[j] = j;
     }
   } else {
@@ -342,7 +344,7 @@ __global__ void k_finish(const DevProb<T>* probs, const int64_t* sig_off, double
         s = warp_sum(s);
       }
       if (lane == 0) {
-        key[j] = j < pr.q ? sqrt(s) : -1.0;
+        key[j] = order_key(j < pr.q ? sqrt(s) : -1.0);
         idx[j] = j;
       }
     }
@@ -355,7 +357,7 @@ __global__ void k_finish(const DevProb<T>* probs, const int64_t* sig_off, double
         int u = t ^ stride;
         if (u > t) {
           bool up = ((t & size) == 0);
-          double ka = key[t], kb = key[u];
+          const unsigned long long ka = key[t], kb = key[u];
           int ia = idx[t], ib = idx[u];
           bool a_first = (ka > kb) || (ka == kb && ia < ib);
           if (a_first != up) {
@@ -371,7 +373,7 @@ __global__ void k_finish(const DevProb<T>* probs, const int64_t* sig_off, double
   }
   const int64_t o = sig_off[blockIdx.x];
   for (int t = threadIdx.x; t < pr.q; t += blockDim.x) {
-    sig[o + t] = key[t];
+    sig[o + t] = order_value(key[t]);
     perm[o + t] = idx[t];
   }
 }

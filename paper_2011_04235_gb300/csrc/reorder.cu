@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(CS_THREADS) k_compact_small(const uint8_t* act
 // ascending compaction) and are distinct, this is exactly the stable sort by
 // key that radix_sort_pairs computes.
 constexpr int SS_THREADS = 1024;
-constexpr int64_t SS_MAX = 16384;
+constexpr int64_t SS_MAX = 2048;   // beyond it the network's n log^2 n shared-memory traffic loses to the radix passes
 __global__ void __launch_bounds__(SS_THREADS) k_sort_small(uint32_t* keys, uint32_t* ids, int n, int np2) {
   extern __shared__ unsigned long long sk[];
   for (int i = threadIdx.x; i < np2; i += SS_THREADS)
