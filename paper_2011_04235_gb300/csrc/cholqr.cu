@@ -6,6 +6,7 @@
 // warp reduction: here the dependent chain is c / 32 block steps, each a
 // 32-step chain inside one warp followed by work spread over the CTA.
 #include <algorithm>
+#include <cstdlib>
 #include <cstdio>
 
 #include "cholqr.cuh"
@@ -287,173 +288,6 @@ __global__ void __launch_bounds__(1024) k_chol_drop_blocked(float* G, int c, flo
 }
 
 
-// ------------------------------------------------------------------------
-// FP64 Cholesky of the residual Gram with dependent directions dropped, in
-// natural column order (no pivoting), blocked by 32 columns over the whole
-// GPU: per block column, one warp factors the 32 x 32 diagonal block of the
-// Schur complement in registers and inverts it, the panel below takes
-// L21 = G21 L11^-T with one thread per entry, and the trailing lower triangle
-// takes the panel's rank-32 update with one thread per entry.  A column whose
-// Schur pivot is <= thr = tol^2 max_t dn[t] is dropped (zero column of L).
-constexpr int UC_NB = 32;
-
-__global__ void __launch_bounds__(32) k_uchol_diag(const double* __restrict__ G, int c, int t0,
-                                                   const double* __restrict__ dn, double tol, double* thr_p,
-                                                   double* __restrict__ L, double* __restrict__ Linv11,
-                                                   int32_t* __restrict__ kept_nat) {
-  __shared__ double Ls[UC_NB][UC_NB + 1];
-  __shared__ int keep_s[UC_NB];
-  const int lane = threadIdx.x;
-  double thr;
-  if (t0 == 0) {
-    double mx = 0.0;
-    for (int i = lane; i < c; i += 32) mx = fmax(mx, dn[i]);
-#pragma unroll
-    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    thr = tol * tol * mx;
-    if (lane == 0) *thr_p = thr;
-  } else {
-    thr = *thr_p;
-  }
-  const int nb = min(UC_NB, c - t0);
-  double a[UC_NB];   // row `lane` of the block
-#pragma unroll
-  for (int i = 0; i < UC_NB; ++i)
-    a[i] = (i <= lane && lane < nb && i < nb) ? G[int64_t(t0 + lane) * c + t0 + i] : 0.0;
-  unsigned km = 0;
-#pragma unroll
-  for (int j = 0; j < UC_NB; ++j) {
-    const double d = __shfl_sync(0xffffffffu, a[j], j);
-    const bool keep = j < nb && d > thr;
-    const double ljj = keep ? sqrt(d) : 0.0;
-    const double r = keep ? 1.0 / ljj : 0.0;
-    if (lane == j)
-      a[j] = ljj;
-    else if (lane > j)
-      a[j] *= r;
-    if (keep) {
-      km |= 1u << j;
-#pragma unroll
-      for (int i = j + 1; i < UC_NB; ++i) {
-        const double lij = __shfl_sync(0xffffffffu, a[j], i);   // L[i, j]
-        if (lane >= i) a[i] = fma(-a[j], lij, a[i]);
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < UC_NB; ++i) {
-    const double v = (i <= lane && lane < nb) ? a[i] : 0.0;
-    Ls[lane][i] = v;
-    if (lane < nb && i < nb) L[int64_t(t0 + lane) * c + t0 + i] = v;
-  }
-  keep_s[lane] = int((km >> lane) & 1u);
-  if (lane < nb) kept_nat[t0 + lane] = keep_s[lane];
-  __syncwarp();
-  // inverse of L11 restricted to the kept columns: lane j forms column j
-  const int j = lane;
-  const bool colk = j < nb && keep_s[j];
-  double x[UC_NB];
-#pragma unroll
-  for (int i = 0; i < UC_NB; ++i) {
-    double sacc = (i == j) ? 1.0 : 0.0;
-#pragma unroll
-    for (int l = 0; l < i; ++l) sacc = fma(-Ls[i][l], x[l], sacc);
-    x[i] = (colk && i < nb && keep_s[i] && i >= j) ? sacc / Ls[i][i] : 0.0;
-  }
-#pragma unroll
-  for (int i = 0; i < UC_NB; ++i) Linv11[i * UC_NB + j] = x[i];
-}
-
-// L[i, t0 + j] = sum_{q <= j} G[i, t0 + q] Linv11[j, q] for the rows below
-// the block (i >= t0 + nb), one thread per entry (warp = one row).
-__global__ void __launch_bounds__(256) k_uchol_panel(const double* __restrict__ G, int c, int t0,
-                                                     const double* __restrict__ Linv11, double* __restrict__ L) {
-  __shared__ double Li[UC_NB][UC_NB + 1];
-  for (int e = threadIdx.x; e < UC_NB * UC_NB; e += blockDim.x) Li[e / UC_NB][e % UC_NB] = Linv11[e];
-  __syncthreads();
-  const int nb = min(UC_NB, c - t0);
-  const int r0 = t0 + nb;
-  const int64_t row = r0 + int64_t(blockIdx.x) * (blockDim.x / 32) + (threadIdx.x >> 5);
-  const int j = threadIdx.x & 31;
-  if (row >= c || j >= nb) return;
-  const double* g = G + row * c + t0;
-  double s0 = 0.0, s1 = 0.0;
-  int q = 0;
-  for (; q + 2 <= j + 1; q += 2) {
-    s0 = fma(g[q], Li[j][q], s0);
-    s1 = fma(g[q + 1], Li[j][q + 1], s1);
-  }
-  if (q <= j) s0 = fma(g[q], Li[j][q], s0);
-  L[row * c + t0 + j] = s0 + s1;
-}
-
-// G[i, l] -= sum_{q < nb} L[i, t0 + q] L[l, t0 + q] for t0 + nb <= l <= i < c.
-__global__ void k_uchol_trailing(double* __restrict__ G, int c, int t0, const double* __restrict__ L) {
-  const int nb = min(UC_NB, c - t0);
-  const int r0 = t0 + nb, nt = c - r0;
-  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (e >= int64_t(nt) * nt) return;
-  const int i = r0 + int(e / nt), l = r0 + int(e % nt);
-  if (l > i) return;
-  const double* Lii = L + int64_t(i) * c + t0;
-  const double* Lll = L + int64_t(l) * c + t0;
-  double s = 0.0;
-#pragma unroll 8
-  for (int q = 0; q < nb; ++q) s = fma(Lii[q], Lll[q], s);
-  G[int64_t(i) * c + l] -= s;
-}
-
-// piv = the kept columns in ascending order, kept[t] = (t < rank),
-// state[1] = rank (one CTA, c <= 1024 * 4).
-__global__ void __launch_bounds__(1024) k_uchol_piv(const int32_t* __restrict__ kept_nat, int c, int32_t* piv,
-                                                    int32_t* kept, int32_t* state) {
-  __shared__ int wsum[32];
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int E = (c + 1023) / 1024;
-  const int i0 = tid * E;
-  int own = 0;
-  for (int e = 0; e < E; ++e)
-    if (i0 + e < c) own += kept_nat[i0 + e];
-  int inc = own;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += t;
-  }
-  if (lane == 31) wsum[w] = inc;
-  __syncthreads();
-  if (w == 0) {
-    const int x = wsum[lane];
-    int xi = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, xi, o);
-      if (lane >= o) xi += t;
-    }
-    wsum[lane] = xi - x;
-    if (lane == 31) state[1] = xi;
-  }
-  __syncthreads();
-  int p = wsum[w] + inc - own;
-  for (int e = 0; e < E; ++e)
-    if (i0 + e < c && kept_nat[i0 + e]) piv[p++] = i0 + e;
-  __syncthreads();
-  const int rank = state[1];
-  for (int t = tid; t < c; t += 1024) {
-    kept[t] = t < rank ? 1 : 0;
-    if (t >= rank) piv[t] = -1;
-  }
-}
-
-// Lo[i, t] = L[i, piv[t]] for t < rank, zero beyond.
-__global__ void k_uchol_lo(const double* __restrict__ L, const int32_t* __restrict__ piv,
-                           const int32_t* __restrict__ state, int c, double* __restrict__ Lo) {
-  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (e >= int64_t(c) * c) return;
-  const int i = int(e / c), t = int(e % c);
-  Lo[e] = t < state[1] ? L[int64_t(i) * c + piv[t]] : 0.0;
-}
-
 }  // namespace
 
 template <typename T>
@@ -481,31 +315,6 @@ void chol_drop_blocked(cudaStream_t st, float* G, int c, float tol, int32_t* kep
   const size_t smem = chol_drop_blocked_smem(c);
   if (smem > 48 * 1024) allow_max_dynamic_smem((const void*)k_chol_drop_blocked);
   k_chol_drop_blocked<<<1, 1024, smem, st>>>(G, c, tol, kept, rank);
-  CK_LAUNCH();
-}
-
-void chol64_drop_unpivoted(cudaStream_t st, double* G, int c, const double* dn, double tol, double* Lo,
-                           int32_t* piv, int32_t* kept, int32_t* state) {
-  if (c <= 0) return;
-  if (c > 4096) fail(FASTPI_ERR_ARG, "Cholesky: too many columns");
-  DArr<double> L(int64_t(c) * c, st), Linv11(UC_NB * UC_NB, st), thr(1, st);
-  DArr<int32_t> kept_nat(c, st);
-  CK(cudaMemsetAsync(L.get(), 0, size_t(c) * c * sizeof(double), st));
-  for (int t0 = 0; t0 < c; t0 += UC_NB) {
-    k_uchol_diag<<<1, 32, 0, st>>>(G, c, t0, dn, tol, thr.get(), L.get(), Linv11.get(), kept_nat.get());
-    CK_LAUNCH();
-    const int nb = std::min(UC_NB, c - t0), rows = c - t0 - nb;
-    if (rows > 0) {
-      k_uchol_panel<<<unsigned((rows + 7) / 8), 256, 0, st>>>(G, c, t0, Linv11.get(), L.get());
-      CK_LAUNCH();
-      const int64_t nt2 = int64_t(rows) * rows;
-      k_uchol_trailing<<<unsigned((nt2 + 255) / 256), 256, 0, st>>>(G, c, t0, L.get());
-      CK_LAUNCH();
-    }
-  }
-  k_uchol_piv<<<1, 1024, 0, st>>>(kept_nat.get(), c, piv, kept, state);
-  CK_LAUNCH();
-  k_uchol_lo<<<unsigned((int64_t(c) * c + 255) / 256), 256, 0, st>>>(L.get(), piv, state, c, Lo);
   CK_LAUNCH();
 }
 

@@ -20,14 +20,6 @@ size_t trinv_blocked_smem(int c, size_t elem);
 // chol_drop_blocked_smem(c) bytes plus 13 KB of static shared memory.
 void chol_drop_blocked(cudaStream_t st, float* G, int c, float tol, int32_t* kept, int32_t* rank);
 size_t chol_drop_blocked_smem(int c);
-// FP64 Cholesky of the c x c Gram G (row-major, full symmetric; overwritten
-// by Schur complements) with dependent directions dropped, in natural column
-// order (no pivoting): a column whose Schur pivot is <= tol^2 max_t dn[t] gets
-// a zero column of L.  Outputs in the layout of the pivoted panel kernels:
-// piv[t] = the t-th kept column (ascending), kept[t] = (t < rank), state[1] =
-// rank, Lo[i, t] = L[i, piv[t]] for t < rank (zero beyond).  c <= 4096.
-void chol64_drop_unpivoted(cudaStream_t st, double* G, int c, const double* dn, double tol, double* Lo,
-                           int32_t* piv, int32_t* kept, int32_t* state);
 // Instrumented builds (FASTPI_PHASE_CLOCKS): prints the accumulated phase
 // clocks of chol_drop_blocked to stderr and resets them; no-op otherwise.
 void chol_drop_phase_report(const char* tag);

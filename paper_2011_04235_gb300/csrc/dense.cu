@@ -38,9 +38,14 @@ __global__ void __launch_bounds__(NT) k_gemm(int64_t M, int64_t N, int64_t K, in
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 
-  for (int64_t k0 = k_begin; k0 < k_end; k0 += BK) {
+  // the next K-slice is read into registers while the current one is
+  // multiplied out of shared memory (the global loads' latency overlaps the
+  // multiply-adds; the arithmetic and its order are unchanged)
+  constexpr int EA = (BM * BK) / NT, EB = (BN * BK) / NT;
+  T ra[EA], rb[EB];
+  auto load = [&](int64_t k0) {
 #pragma unroll
-    for (int e = 0; e < (BM * BK) / NT; ++e) {
+    for (int e = 0; e < EA; ++e) {
       int lin = tid + NT * e;
       int i, kk;
       if (TA) {
@@ -51,12 +56,10 @@ __global__ void __launch_bounds__(NT) k_gemm(int64_t M, int64_t N, int64_t K, in
         i = lin / BK;
       }
       int64_t gi = m0 + i, gk = k0 + kk;
-      T v = T(0);
-      if (gi < M && gk < k_end) v = T(TA ? A[gk * lda + gi] : A[gi * lda + gk]);
-      As[kk][i] = v;
+      ra[e] = (gi < M && gk < k_end) ? T(TA ? A[gk * lda + gi] : A[gi * lda + gk]) : T(0);
     }
 #pragma unroll
-    for (int e = 0; e < (BN * BK) / NT; ++e) {
+    for (int e = 0; e < EB; ++e) {
       int lin = tid + NT * e;
       int j, kk;
       if (TB) {
@@ -67,11 +70,32 @@ __global__ void __launch_bounds__(NT) k_gemm(int64_t M, int64_t N, int64_t K, in
         kk = lin / BN;
       }
       int64_t gj = n0 + j, gk = k0 + kk;
-      T v = T(0);
-      if (gj < N && gk < k_end) v = T(TB ? B[gj * ldb + gk] : B[gk * ldb + gj]);
-      Bs[kk][j] = v;
+      rb[e] = (gj < N && gk < k_end) ? T(TB ? B[gj * ldb + gk] : B[gk * ldb + gj]) : T(0);
     }
+  };
+  auto store = [&] {
+#pragma unroll
+    for (int e = 0; e < EA; ++e) {
+      int lin = tid + NT * e;
+      if (TA)
+        As[lin / BM][lin % BM] = ra[e];
+      else
+        As[lin % BK][lin / BK] = ra[e];
+    }
+#pragma unroll
+    for (int e = 0; e < EB; ++e) {
+      int lin = tid + NT * e;
+      if (TB)
+        Bs[lin % BK][lin / BK] = rb[e];
+      else
+        Bs[lin / BN][lin % BN] = rb[e];
+    }
+  };
+  if (k_begin < k_end) load(k_begin);
+  for (int64_t k0 = k_begin; k0 < k_end; k0 += BK) {
+    store();
     __syncthreads();
+    if (k0 + BK < k_end) load(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       T a[4], b[4];

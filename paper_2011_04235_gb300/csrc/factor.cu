@@ -636,14 +636,6 @@ void pchol_phase_report(const char* tag) {
 #endif
 }
 
-// Whether the mixed form factors the residual Gram with diagonal pivoting
-// (default; the FP64 form always does, as the oracle's QR with column
-// pivoting) or with the unpivoted blocked Cholesky (FASTPI_MIXED_PIVOT=0).
-bool mixed_pivoted_cholesky() {
-  const char* e = std::getenv("FASTPI_MIXED_PIVOT");
-  return !(e && e[0] == '0' && e[1] == 0);
-}
-
 // Whether the core SVD runs on K^T, i.e. one-sided Jacobi orthogonalises the
 // rows of K = [[diag(sigma), P], [0, R_R]] rather than its columns (default;
 // FASTPI_CORE_TRANSPOSE=0 takes the columns).  Two rows i, i' < k of K meet
@@ -905,16 +897,7 @@ struct Phase {
     };
     gram(D.get(), G.get());
     const size_t pan_bytes = size_t(c) * PCHOL_PS * sizeof(double) + size_t(c) * (sizeof(double) + sizeof(int));
-    if (sizeof(T) == 4 && !mixed_pivoted_cholesky() && c <= 4096) {
-      // mixed form: the blocked FP64 Cholesky without pivoting, spread over
-      // the GPU (the drop rule is the same; the kept directions are taken in
-      // column order instead of by decreasing remaining norm)
-      DArr<int32_t> pstate(2, st);
-      CK(cudaMemsetAsync(pstate.get(), 0, 8, st));
-      chol64_drop_unpivoted(st, G.get(), int(c), dn.get(), drop_tol, Lo.get(), piv.get(), kept.get(), pstate.get());
-      k_gather_lp<<<g1(c * c), 256, 0, st>>>(Lo.get(), piv.get(), pstate.get(), int(c), Lp.get(), rk.get());
-      CK_LAUNCH();
-    } else if (pan_bytes <= 200 * 1024) {
+    if (pan_bytes <= 200 * 1024) {
       // blocked: panels of PCHOL_NB columns in one CTA, each followed by the
       // Schur-complement update of the columns after it over every SM
       DArr<double> dd(c, st);
