@@ -283,28 +283,37 @@ __device__ __forceinline__ int32_t uf_find(int32_t* parent, int32_t x) {
   return x;
 }
 
-__global__ void k_cc_hook(const int32_t* nz_row, const int32_t* col, const uint8_t* act, int64_t m, int64_t nnz,
-                          int32_t* parent, unsigned* status) {
-  int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (e >= nnz) return;
-  int32_t i = nz_row[e];
-  int32_t j = int32_t(m) + col[e];
-  if (!act[i] || !act[j]) return;
-  int32_t ru = uf_find(parent, i), rv = uf_find(parent, j);
-  int guard = 0;
-  while (ru != rv) {
-    if (ru > rv) {
-      int32_t t = ru;
-      ru = rv;
-      rv = t;
-    }
-    int32_t old = atomicCAS(&parent[rv], rv, ru);
-    if (old == rv) break;
-    rv = uf_find(parent, old);
-    ru = uf_find(parent, ru);
-    if (++guard > (1 << 20)) {
-      atomicOr(status, ST_UF_RETRY_CAP);
-      break;
+// Union-find hooking of the active edges, by rows: one warp per row i, the
+// lanes over its nonzeros; the larger root is always linked under the smaller.
+// A row that is no longer active (a hub or a component placed earlier) is
+// skipped with one load instead of one per nonzero, which matters more with
+// every iteration.  Whatever order the hooks land in, every component ends up
+// rooted at its minimum id.
+__global__ void k_cc_hook_rows(const int64_t* rowptr, const int32_t* col, const uint8_t* act, int64_t m,
+                               int32_t* parent, unsigned* status) {
+  const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= m || !act[w]) return;
+  const int32_t i = int32_t(w);
+  for (int64_t e = rowptr[w] + lane; e < rowptr[w + 1]; e += 32) {
+    const int32_t j = int32_t(m) + col[e];
+    if (!act[j]) continue;
+    int32_t ru = uf_find(parent, i), rv = uf_find(parent, j);
+    int guard = 0;
+    while (ru != rv) {
+      if (ru > rv) {
+        const int32_t t = ru;
+        ru = rv;
+        rv = t;
+      }
+      const int32_t old = atomicCAS(&parent[rv], rv, ru);
+      if (old == rv) break;
+      rv = uf_find(parent, old);
+      ru = uf_find(parent, ru);
+      if (++guard > (1 << 20)) {
+        atomicOr(status, ST_UF_RETRY_CAP);
+        break;
+      }
     }
   }
 }
@@ -479,11 +488,6 @@ void run_reorder(fastpi_ctx* h, double k, Reordering& R) {
   DArr<uint8_t> act(N, st);
   CK(cudaMemsetAsync(act.get(), 1, size_t(N), st));
   DArr<int32_t> deg(N, st), parent(N, st), label(N, st), cntT(N, st), cntF(N, st);
-  DArr<int32_t> nz_row(nnz, st);
-  if (nnz > 0) {
-    k_row_of_nz<<<nblk(m * 32), BS, 0, st>>>(h->rowptr, m, nz_row);
-    CK_LAUNCH();
-  }
   const int64_t cap = N + 1;
   // scratch of the main stream (rows, components) and of the side stream (columns)
   DArr<int32_t> flags(cap, st), pos(cap, st), dcount(4, st);
@@ -559,7 +563,7 @@ void run_reorder(fastpi_ctx* h, double k, Reordering& R) {
     CK_LAUNCH();
     side.finish(st);
     if (nnz > 0) {
-      k_cc_hook<<<nblk(nnz), BS, 0, st>>>(nz_row, h->col, act, m, nnz, parent, h->dstatus);
+      k_cc_hook_rows<<<nblk(m * 32), BS, 0, st>>>(h->rowptr, h->col, act, m, parent, h->dstatus);
       CK_LAUNCH();
     }
     k_cc_label<<<nblk(N), BS, 0, st>>>(act, N, parent, label, m, cntT, cntF);
